@@ -1,0 +1,522 @@
+"""FP64 CPU oracle of the 3D SIFT detector and the BRIEF / RRIEF descriptors.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this module.  The CUDA
+library never calls it, and it shares no code with the CUDA path: both sides only
+receive the same seeded input volumes from ``workloads/``.
+
+Every function follows the paper (Carluer et al., "GPU optimization of the 3D
+Scale-invariant Feature Transform Algorithm and a Novel BRIEF-inspired 3D Fast
+Descriptor", arXiv 2112.10258) in plain numpy float64, step by step, with no
+blocking or fusion:
+
+* Gaussian scale space by recursive separable Gaussian filtering - Sec. 2 (Related
+  Work, scale space generated recursively with separable 1D filters), Sec. 2.2.2
+  "Gaussian Convolution" (three separable 1D convolutions in x, y, z), Fig. 8
+  caption (6 convolutions per octave with increasing filter size).
+* Sub-sampling by two: one output voxel from 8 input voxels - Sec. 2.2.2
+  "Sub-sampling".
+* Difference of Gaussians DoG(sigma) = I(sigma) - I(kappa sigma) - Sec. 2.2.2
+  "Difference-of-Gaussian".
+* 4D peak detection by the sum of signs over the 27+26+27 = 80 neighbours in three
+  consecutive DoG volumes; peaks are +80, valleys -80, the cut is tunable - Sec.
+  2.2.2 "4D Peak Detection" (sum-of-signs equation).  The extremum search here is
+  the brute-force neighbour comparison the paper's CPU method uses (Sec. 4.4).
+* BRIEF (binarised point-pair differences of a blurred patch) and RRIEF (the same
+  differences, rank ordered) - Sec. 2.2.3; point-pair method 3 (p1 ~ N(0, s),
+  p2 ~ N(p1, s)); pre-blur sigma 0.95 (Sec. 4.5).
+
+Readings where the paper is silent (each also listed in the design doc):
+
+* sigma0 = 1.6, sigma_in = 0.5, S = 3 scales per octave, S + 3 = 6 Gaussian levels
+  with sigma_s = sigma0 * 2^(s/S); octave 0 starts with a blur of
+  sqrt(sigma0^2 - sigma_in^2); level s is level s-1 blurred by
+  sqrt(sigma_s^2 - sigma_{s-1}^2); octave o+1 starts from the sub-sample of level S.
+* Discrete kernel w_k ~ exp(-k^2 / 2 sigma^2), |k| <= ceil(4 sigma), unit sum;
+  clamp-to-edge boundary.
+* DoG D_s = G_s - G_{s+1}; detection on D_1..D_S, interior voxels (border >= 1).
+* Contrast test |D| >= t_c and a 3D Hessian curvature test (not in the paper).
+* n = 64 point pairs, offsets in units of the keypoint's scale, clipped to
+  |u|_inf <= 4 by resampling; pattern drawn with SplitMix64 + Box-Muller.
+
+Arrays are numpy (nz, ny, nx), x fastest.
+
+Parity bookkeeping: each decision of the detector is a comparison.  A comparison
+whose FP64 margin is below ``REL_TOL`` x local magnitude is a *near tie*; the
+oracle reports the voxels whose keypoint/non-keypoint outcome could flip under
+such near ties (``DetectResult.uncertain``), so a float32 implementation may
+differ from this oracle there and nowhere else.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+REL_TOL = 1e-5  # operand-margin tolerance relative to the local pyramid magnitude
+
+KEYPOINT_DTYPE = np.dtype([
+    ("octave", np.int32), ("scale", np.int32),
+    ("ix", np.int32), ("iy", np.int32), ("iz", np.int32),
+    ("polarity", np.int32), ("sign_sum", np.int32), ("dog", np.float64),
+    ("x", np.float64), ("y", np.float64), ("z", np.float64), ("sigma", np.float64),
+])
+
+
+@dataclass
+class Params:
+    sigma0: float = 1.6
+    sigma_in: float = 0.5
+    scales_per_octave: int = 3
+    min_octave_dim: int = 16
+    max_octaves: int = 0          # 0 = until an octave would be smaller than min_octave_dim
+    sign_sum_min: int = 80        # |sum of signs| cut; 80 = strict extremum
+    border: int = 1
+    contrast_thresh: float = 0.005
+    curvature_r: float = 10.0
+    trunc: float = 4.0
+    desc_blur_sigma: float = 0.95
+    desc_method: int = 3
+    pattern_seed: int = 0x5EED5EED
+
+
+# ----------------------------------------------------------------------------------
+# Scale schedule (Sec. 2.2.2 Gaussian Convolution; Fig. 8 caption)
+# ----------------------------------------------------------------------------------
+
+def level_sigmas(p: Params) -> list[float]:
+    """sigma_s = sigma0 * 2^(s/S) for the S+3 Gaussian levels of an octave."""
+    S = p.scales_per_octave
+    return [p.sigma0 * 2.0 ** (s / S) for s in range(S + 3)]
+
+
+def initial_sigma(p: Params) -> float:
+    """Blur that brings an input assumed at sigma_in up to sigma0."""
+    return math.sqrt(p.sigma0 ** 2 - p.sigma_in ** 2)
+
+
+def increment_sigmas(p: Params) -> list[float]:
+    """Incremental blur from level s-1 to level s, s = 1..S+2."""
+    sig = level_sigmas(p)
+    return [math.sqrt(sig[s] ** 2 - sig[s - 1] ** 2) for s in range(1, len(sig))]
+
+
+def octave_shapes(p: Params, shape_zyx) -> list[tuple[int, int, int]]:
+    """Octave o has dims floor(dims / 2^o); keep octaves while min dim >= min_octave_dim."""
+    shapes = []
+    cur = tuple(int(v) for v in shape_zyx)
+    while min(cur) >= p.min_octave_dim and (p.max_octaves <= 0 or len(shapes) < p.max_octaves):
+        shapes.append(cur)
+        cur = tuple(v // 2 for v in cur)
+    return shapes
+
+
+# ----------------------------------------------------------------------------------
+# Gaussian convolution (Sec. 2.2.2: three separable 1D convolutions in x, y, z)
+# ----------------------------------------------------------------------------------
+
+def gaussian_radius(sigma: float, trunc: float = 4.0) -> int:
+    return int(math.ceil(trunc * sigma))
+
+
+def gaussian_taps(sigma: float, trunc: float = 4.0) -> np.ndarray:
+    """Sampled Gaussian N(0, sigma^2) on k = -R..R, R = ceil(trunc*sigma), unit sum."""
+    R = gaussian_radius(sigma, trunc)
+    k = np.arange(-R, R + 1, dtype=np.float64)
+    w = np.exp(-(k * k) / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def conv1d_clamp(vol: np.ndarray, taps: np.ndarray, axis: int) -> np.ndarray:
+    """out[i] = sum_k taps[k] * vol[clamp(i + k - R)] along ``axis`` (edge replicate)."""
+    R = (len(taps) - 1) // 2
+    n = vol.shape[axis]
+    idx = np.arange(n)
+    out = np.zeros(vol.shape, np.float64)
+    for j in range(len(taps)):
+        src = np.clip(idx + (j - R), 0, n - 1)
+        out += taps[j] * np.take(vol, src, axis=axis)
+    return out
+
+
+def blur3d(vol: np.ndarray, sigma: float, trunc: float = 4.0) -> np.ndarray:
+    """Separable 3D Gaussian: an x pass, then a y pass, then a z pass."""
+    taps = gaussian_taps(sigma, trunc)
+    out = conv1d_clamp(np.asarray(vol, np.float64), taps, axis=2)
+    out = conv1d_clamp(out, taps, axis=1)
+    return conv1d_clamp(out, taps, axis=0)
+
+
+# ----------------------------------------------------------------------------------
+# Sub-sampling (Sec. 2.2.2: 8 input voxels give one output voxel)
+# ----------------------------------------------------------------------------------
+
+def subsample2(vol: np.ndarray) -> np.ndarray:
+    """Mean of each 2x2x2 block; a trailing odd voxel on an axis is dropped."""
+    Z, Y, X = (v // 2 for v in vol.shape)
+    v = np.asarray(vol, np.float64)[: 2 * Z, : 2 * Y, : 2 * X]
+    acc = np.zeros((Z, Y, X), np.float64)
+    for a, b, c in itertools.product((0, 1), repeat=3):
+        acc += v[a::2, b::2, c::2]
+    return acc / 8.0
+
+
+# ----------------------------------------------------------------------------------
+# Pyramid: Gaussian levels and DoG (Sec. 2.2.2 "Difference-of-Gaussian")
+# ----------------------------------------------------------------------------------
+
+@dataclass
+class Pyramid:
+    G: list = field(default_factory=list)   # G[o][s], s = 0..S+2
+    D: list = field(default_factory=list)   # D[o][s] = G[o][s] - G[o][s+1], s = 0..S+1
+
+
+def input_to_float(vol: np.ndarray) -> np.ndarray:
+    """float inputs are used as they are; uint8 codes map to [0, 1] by /255."""
+    if vol.dtype == np.uint8:
+        return vol.astype(np.float64) / 255.0
+    return np.asarray(vol, np.float64)
+
+
+def build_pyramid(vol: np.ndarray, p: Params) -> Pyramid:
+    shapes = octave_shapes(p, vol.shape)
+    incs = increment_sigmas(p)
+    pyr = Pyramid()
+    S = p.scales_per_octave
+    for o in range(len(shapes)):
+        if o == 0:
+            g0 = blur3d(input_to_float(vol), initial_sigma(p), p.trunc)
+        else:
+            g0 = subsample2(pyr.G[o - 1][S])
+        levels = [g0]
+        for s in range(1, S + 3):
+            levels.append(blur3d(levels[-1], incs[s - 1], p.trunc))
+        pyr.G.append(levels)
+        pyr.D.append([levels[s] - levels[s + 1] for s in range(S + 2)])
+    return pyr
+
+
+# ----------------------------------------------------------------------------------
+# 4D peak detection by sum of signs (Sec. 2.2.2 "4D Peak Detection"), contrast and
+# curvature tests, and near-tie bookkeeping.
+# ----------------------------------------------------------------------------------
+
+NEIGHBOUR_OFFSETS = [d for d in itertools.product((-1, 0, 1), repeat=3)]  # (dz, dy, dx)
+
+
+@dataclass
+class DetectResult:
+    keypoints: np.ndarray                       # KEYPOINT_DTYPE, canonical order
+    uncertain: set = field(default_factory=set)  # {(o, s, iz, iy, ix)} with a near tie
+    n_candidates: int = 0
+    pyramid: Pyramid | None = None
+
+
+def _robust(value: np.ndarray, bound: np.ndarray):
+    """Decision value > 0 with first-order error ``bound``.
+    Returns (robust_true, robust_false)."""
+    return value > bound, value < -bound
+
+
+def sum_of_signs(centre: np.ndarray, neighbours: list[np.ndarray]) -> np.ndarray:
+    """f = sum over the neighbours of sign(D_centre - D_neighbour)."""
+    S = np.zeros(centre.shape, np.int64)
+    for nb in neighbours:
+        S += np.sign(centre - nb).astype(np.int64)
+    return S
+
+
+def _hessian(Ds, cz, cy, cx):
+    """Central-difference Hessian of D_s at the candidate voxels (entries of H)."""
+    def d(dz, dy, dx):
+        return Ds[cz + dz, cy + dy, cx + dx]
+    c = d(0, 0, 0)
+    hxx = d(0, 0, 1) + d(0, 0, -1) - 2.0 * c
+    hyy = d(0, 1, 0) + d(0, -1, 0) - 2.0 * c
+    hzz = d(1, 0, 0) + d(-1, 0, 0) - 2.0 * c
+    hxy = (d(0, 1, 1) - d(0, -1, 1) - d(0, 1, -1) + d(0, -1, -1)) / 4.0
+    hxz = (d(1, 0, 1) - d(-1, 0, 1) - d(1, 0, -1) + d(-1, 0, -1)) / 4.0
+    hyz = (d(1, 1, 0) - d(-1, 1, 0) - d(1, -1, 0) + d(-1, -1, 0)) / 4.0
+    return hxx, hyy, hzz, hxy, hxz, hyz
+
+
+def curvature_test(h, polarity, r, eta=None):
+    """Curvature test on H' = -polarity * H (a maximum has a negative definite H):
+    H' positive definite by Sylvester's criterion (leading minors > 0) and
+    tr(H')^3 * r^2 < (2r+1)^3 * det(H'), the 3D extension of the 2D edge test with
+    eigenvalue ratio r (eigenvalues (a, ra, ra) give equality).
+
+    With ``eta`` (per-DoG-value error allowance) also returns robust-true /
+    robust-false masks from first-order error bounds of each quantity."""
+    sgn = -polarity.astype(np.float64)
+    a, b, c, xy, xz, yz = (sgn * v for v in h)
+    m1 = a
+    m2 = a * b - xy * xy
+    det = a * (b * c - yz * yz) - xy * (xy * c - yz * xz) + xz * (xy * yz - b * xz)
+    tr = a + b + c
+    k1 = (2.0 * r + 1.0) ** 3
+    k2 = r * r
+    g = k1 * det - k2 * tr ** 3
+    ok = (m1 > 0) & (m2 > 0) & (det > 0) & (g > 0)
+    if eta is None:
+        return ok
+    da = 4.0 * eta                     # |1| + |-2| + |1| DoG values per diagonal entry
+    do = 1.0 * eta                     # 4 values x 1/4 per off-diagonal entry
+    b_m1 = da
+    b_m2 = np.abs(b) * da + np.abs(a) * da + 2.0 * np.abs(xy) * do
+    cof_a = np.abs(b * c - yz * yz)
+    cof_b = np.abs(a * c - xz * xz)
+    cof_c = np.abs(a * b - xy * xy)
+    cof_xy = 2.0 * np.abs(xy * c - yz * xz)
+    cof_xz = 2.0 * np.abs(xy * yz - b * xz)
+    cof_yz = 2.0 * np.abs(a * yz - xy * xz)
+    b_det = (cof_a + cof_b + cof_c) * da + (cof_xy + cof_xz + cof_yz) * do
+    b_g = k1 * b_det + 3.0 * k2 * tr * tr * (3.0 * da)
+    parts = [(m1, b_m1), (m2, b_m2), (det, b_det), (g, b_g)]
+    robust_true = np.ones(m1.shape, bool)
+    robust_false = np.zeros(m1.shape, bool)
+    for v, bd in parts:
+        t, f = _robust(v, bd)
+        robust_true &= t
+        robust_false |= f
+    return ok, robust_true, robust_false
+
+
+def detect(vol: np.ndarray, p: Params, keep_pyramid: bool = True) -> DetectResult:
+    pyr = build_pyramid(vol, p)
+    S = p.scales_per_octave
+    sig = level_sigmas(p)
+    rows = []
+    uncertain = set()
+    n_cand = 0
+    for o in range(len(pyr.G)):
+        G, D = pyr.G[o], pyr.D[o]
+        Z, Y, X = D[0].shape
+        b = p.border
+        if Z < 2 * b + 1 or Y < 2 * b + 1 or X < 2 * b + 1:
+            continue
+        gmax = max(float(np.max(np.abs(g))) for g in G)
+        tau_max = REL_TOL * gmax          # no local tolerance exceeds this
+        T = p.sign_sum_min
+        for s in range(1, S + 1):
+            Ds = D[s]
+            inner = Ds[b:Z - b, b:Y - b, b:X - b]
+            # Necessary conditions, evaluated on every interior voxel: the contrast
+            # test and the 26 neighbours in D_s, each counted as a near tie when
+            # within tau_max.  A voxel that fails either even with every near tie
+            # resolved in its favour can neither be a keypoint nor be uncertain.
+            maybe = np.abs(inner) >= p.contrast_thresh - tau_max
+            s26 = np.zeros(inner.shape, np.int16)
+            n26 = np.zeros(inner.shape, np.int16)
+            for dz, dy, dx in NEIGHBOUR_OFFSETS:
+                if dz == 0 and dy == 0 and dx == 0:
+                    continue
+                nb = Ds[b + dz:Z - b + dz, b + dy:Y - b + dy, b + dx:X - b + dx]
+                diff = inner - nb
+                near = np.abs(diff) < tau_max
+                s26 += np.where(near, 0, np.sign(diff)).astype(np.int16)
+                n26 += near
+            rest = 54
+            maybe &= (s26 + n26 + rest >= T) | (s26 - n26 - rest <= -T)
+            cz, cy, cx = np.nonzero(maybe)
+            cz, cy, cx = cz + b, cy + b, cx + b
+            if cz.size == 0:
+                continue
+            n_cand += cz.size
+            c = Ds[cz, cy, cx]
+            # local magnitude: largest |G| over the 3x3x3 neighbourhood in the four
+            # Gaussian levels the three DoG volumes are formed from
+            mag = np.zeros(c.shape)
+            for lvl in range(s - 1, s + 3):
+                for dz, dy, dx in NEIGHBOUR_OFFSETS:
+                    mag = np.maximum(mag, np.abs(G[lvl][cz + dz, cy + dy, cx + dx]))
+            tau = REL_TOL * mag
+            # contrast |D| >= t_c
+            con = np.abs(c) >= p.contrast_thresh
+            con_rt = np.abs(c) - p.contrast_thresh >= tau
+            con_rf = p.contrast_thresh - np.abs(c) > tau
+            # sum of signs over the 80 neighbours (27 in D_{s-1}, 26 in D_s, 27 in D_{s+1})
+            Ssum = np.zeros(c.shape, np.int64)
+            S_rob = np.zeros(c.shape, np.int64)
+            n_near = np.zeros(c.shape, np.int64)
+            for lvl in (s - 1, s, s + 1):
+                for dz, dy, dx in NEIGHBOUR_OFFSETS:
+                    if lvl == s and dz == 0 and dy == 0 and dx == 0:
+                        continue
+                    diff = c - D[lvl][cz + dz, cy + dy, cx + dx]
+                    sg = np.sign(diff).astype(np.int64)
+                    near = np.abs(diff) < tau
+                    Ssum += sg
+                    S_rob += np.where(near, 0, sg)
+                    n_near += near
+            ext = np.abs(Ssum) >= T
+            smax, smin = S_rob + n_near, S_rob - n_near
+            ext_rt = (smin >= T) | (smax <= -T)
+            ext_rf = (smax < T) & (smin > -T)
+            polarity = np.where(Ssum > 0, 1, np.where(Ssum < 0, -1, 0))
+            polarity = np.where(S_rob != 0, np.sign(S_rob), polarity).astype(np.int64)
+            # curvature (Hessian) test on D_s, evaluated with the extremum's polarity
+            h = _hessian(Ds, cz, cy, cx)
+            cur, cur_rt, cur_rf = curvature_test(h, polarity, p.curvature_r, eta=tau / 2.0)
+            keep = con & ext & cur
+            rob_false = con_rf | ext_rf | cur_rf
+            rob_true = con_rt & ext_rt & cur_rt
+            unsure = ~rob_false & ~rob_true
+            for i in np.nonzero(unsure)[0]:
+                uncertain.add((o, s, int(cz[i]), int(cy[i]), int(cx[i])))
+            for i in np.nonzero(keep)[0]:
+                ix, iy, iz = int(cx[i]), int(cy[i]), int(cz[i])
+                scale = 2.0 ** o
+                rows.append((o, s, ix, iy, iz, int(polarity[i]), int(Ssum[i]), float(c[i]),
+                             (ix + 0.5) * scale - 0.5, (iy + 0.5) * scale - 0.5,
+                             (iz + 0.5) * scale - 0.5, sig[s] * scale))
+    kps = np.array(rows, dtype=KEYPOINT_DTYPE)
+    kps = sort_keypoints(kps)
+    return DetectResult(kps, uncertain, n_cand, pyr if keep_pyramid else None)
+
+
+def sort_keypoints(kps: np.ndarray) -> np.ndarray:
+    """Canonical order (octave, scale, iz, iy, ix)."""
+    if kps.size == 0:
+        return kps
+    order = np.lexsort((kps["ix"], kps["iy"], kps["iz"], kps["scale"], kps["octave"]))
+    return kps[order]
+
+
+# ----------------------------------------------------------------------------------
+# Point-pair pattern (Sec. 2.2.3, method 3) from SplitMix64 + Box-Muller
+# ----------------------------------------------------------------------------------
+
+MASK64 = (1 << 64) - 1
+SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(state: int) -> tuple[int, int]:
+    """One SplitMix64 step (Steele, Lea & Flood, OOPSLA 2014): returns (new_state, output)."""
+    state = (state + SPLITMIX_GAMMA) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return state, z ^ (z >> 31)
+
+
+class NormalStream:
+    """Standard normals: each draw takes two 53-bit uniforms u, v in (0, 1) and
+    returns sqrt(-2 ln u) * cos(2 pi v) (Box & Muller, 1958)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def uniform(self) -> float:
+        self.state, z = splitmix64(self.state)
+        return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0)
+
+    def normal(self) -> float:
+        u = self.uniform()
+        v = self.uniform()
+        return math.sqrt(-2.0 * math.log(u)) * math.cos(2.0 * math.pi * v)
+
+
+N_PAIRS = 64
+PATTERN_CLIP = 4.0
+
+
+def pattern_method3(seed: int, n_pairs: int = N_PAIRS, clip: float = PATTERN_CLIP) -> np.ndarray:
+    """Method 3: p1 ~ N(0, I), p2 ~ N(p1, I), in units of the keypoint scale; a point
+    with any |coordinate| > clip is redrawn.  Returns (n_pairs, 2, 3) in (x, y, z)."""
+    rng = NormalStream(seed)
+    out = np.zeros((n_pairs, 2, 3))
+    for k in range(n_pairs):
+        while True:
+            p1 = np.array([rng.normal() for _ in range(3)])
+            if np.all(np.abs(p1) <= clip):
+                break
+        while True:
+            p2 = p1 + np.array([rng.normal() for _ in range(3)])
+            if np.all(np.abs(p2) <= clip):
+                break
+        out[k, 0], out[k, 1] = p1, p2
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Descriptors (Sec. 2.2.3): blur, sample point pairs, difference, binarise / rank
+# ----------------------------------------------------------------------------------
+
+def trilinear_clamp(V: np.ndarray, pts: np.ndarray):
+    """Trilinear interpolation of V (Z, Y, X) at points (..., 3) given as (x, y, z)
+    with each coordinate clamped to [0, dim-1].  Returns (values, max |corner|)."""
+    Z, Y, X = V.shape
+    px = np.clip(pts[..., 0], 0.0, X - 1.0)
+    py = np.clip(pts[..., 1], 0.0, Y - 1.0)
+    pz = np.clip(pts[..., 2], 0.0, Z - 1.0)
+    x0, y0, z0 = (np.floor(q).astype(np.int64) for q in (px, py, pz))
+    fx, fy, fz = px - x0, py - y0, pz - z0
+    x1, y1, z1 = np.minimum(x0 + 1, X - 1), np.minimum(y0 + 1, Y - 1), np.minimum(z0 + 1, Z - 1)
+    val = np.zeros(px.shape)
+    mag = np.zeros(px.shape)
+    for zi, wz in ((z0, 1.0 - fz), (z1, fz)):
+        for yi, wy in ((y0, 1.0 - fy), (y1, fy)):
+            for xi, wx in ((x0, 1.0 - fx), (x1, fx)):
+                v = V[zi, yi, xi]
+                val += wz * wy * wx * v
+                mag = np.maximum(mag, np.abs(v))
+    return val, mag
+
+
+def rank_order(d: np.ndarray) -> np.ndarray:
+    """Rank of each element, 0 = smallest; equal values ranked by lower index first."""
+    n = d.shape[-1]
+    ranks = np.zeros(d.shape, np.int64)
+    for k in range(n):
+        less = d < d[..., k:k + 1]
+        equal_before = (d == d[..., k:k + 1]) & (np.arange(n) < k)
+        ranks[..., k] = np.sum(less | equal_before, axis=-1)
+    return ranks
+
+
+@dataclass
+class DescribeResult:
+    brief: np.ndarray      # (n,) uint64, bit k = [d_k > 0]
+    rrief: np.ndarray      # (n, 64) uint8 ranks
+    d: np.ndarray          # (n, 64) float64 point-pair differences
+    mag: np.ndarray        # (n, 64) local magnitude (largest |corner| of both samples)
+
+
+def blurred_level(pyr: Pyramid, o: int, s: int, p: Params) -> np.ndarray:
+    """The keypoint's Gaussian level G_s of octave o, pre-blurred by desc_blur_sigma."""
+    if p.desc_blur_sigma <= 0.0:
+        return pyr.G[o][s]
+    return blur3d(pyr.G[o][s], p.desc_blur_sigma, p.trunc)
+
+
+def describe(pyr: Pyramid, kps: np.ndarray, p: Params, pattern: np.ndarray | None = None,
+             cache: dict | None = None) -> DescribeResult:
+    if pattern is None:
+        pattern = pattern_method3(p.pattern_seed)
+    n = kps.size
+    npair = pattern.shape[0]
+    d = np.zeros((n, npair))
+    mag = np.zeros((n, npair))
+    sig = level_sigmas(p)
+    cache = {} if cache is None else cache
+    for i in range(n):
+        o, s = int(kps["octave"][i]), int(kps["scale"][i])
+        if (o, s) not in cache:
+            cache[(o, s)] = blurred_level(pyr, o, s, p)
+        B = cache[(o, s)]
+        c = np.array([kps["ix"][i], kps["iy"][i], kps["iz"][i]], np.float64)
+        p1 = c + sig[s] * pattern[:, 0, :]
+        p2 = c + sig[s] * pattern[:, 1, :]
+        v1, m1 = trilinear_clamp(B, p1)
+        v2, m2 = trilinear_clamp(B, p2)
+        d[i] = v1 - v2
+        mag[i] = np.maximum(m1, m2)
+    bits = (d > 0).astype(np.uint64)
+    brief = np.zeros(n, np.uint64)
+    for k in range(npair):
+        brief |= bits[:, k] << np.uint64(k)
+    rrief = rank_order(d).astype(np.uint8)
+    return DescribeResult(brief, rrief, d, mag)
