@@ -1,0 +1,267 @@
+/*
+ * sift3d.h - C ABI of the GB300 (sm_103a) 3D SIFT detector and BRIEF/RRIEF
+ * descriptor library.
+ *
+ * The operations follow Carluer et al., "GPU optimization of the 3D
+ * Scale-invariant Feature Transform Algorithm and a Novel BRIEF-inspired 3D Fast
+ * Descriptor" (arXiv 2112.10258):
+ *   - Gaussian scale space by separable x/y/z filtering ........ Sec. 2.2.2
+ *     "Gaussian Convolution"; Fig. 8 (6 convolutions per octave)
+ *   - octave sub-sampling by 2 (8 voxels -> 1) ................. Sec. 2.2.2
+ *     "Sub-sampling"
+ *   - difference of Gaussians DoG = I(sigma) - I(kappa sigma) .. Sec. 2.2.2
+ *     "Difference-of-Gaussian"
+ *   - 4D peak detection by the sum of signs over 80 neighbours . Sec. 2.2.2
+ *     "4D Peak Detection" (sum-of-signs equation, +-80 cut)
+ *   - BRIEF and RRIEF descriptors, point-pair method 3 ......... Sec. 2.2.3;
+ *     pre-blur sigma 0.95 (Sec. 4.5)
+ * The contrast and Hessian curvature tests and the serving calls have no
+ * counterpart in the paper; their definitions are given below.
+ *
+ * Conventions (every function):
+ *   - Return value: SIFT3D_OK (0), SIFT3D_PENDING (1, poll only) or a negative
+ *     SIFT3D_E* code.  No C++ exception crosses this boundary.  The message of
+ *     the last failure on a context is available from sift3d_last_error().
+ *   - Volumes are dense, x fastest: voxel (x, y, z) is at x + nx*(y + ny*z).
+ *     Each dimension must be in [1, 4095].
+ *   - "dev_" pointers are CUDA device pointers owned by the caller; "host"
+ *     pointers are ordinary host memory owned by the caller unless stated.
+ *   - A context is not thread safe: calls on one context must not overlap,
+ *     except sift3d_poll, which may be called from any thread.
+ *   - Work is ordered on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Only the calls that return host
+ *     results (n_out != NULL in detect, poll) wait for the device.
+ */
+#ifndef SIFT3D_H
+#define SIFT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define SIFT3D_OK          0
+#define SIFT3D_PENDING     1   /* sift3d_poll: request not finished yet          */
+#define SIFT3D_EINVAL     -1   /* bad argument or parameter                      */
+#define SIFT3D_ENOMEM     -2   /* device or host allocation failed               */
+#define SIFT3D_ECAPACITY  -3   /* more keypoints than the output capacity        */
+#define SIFT3D_ETIMEDOUT  -4   /* a bounded wait ran out                         */
+#define SIFT3D_ECUDA      -5   /* a CUDA runtime call failed                     */
+#define SIFT3D_ENOTFOUND  -6   /* unknown ticket                                 */
+#define SIFT3D_EBUDGET    -7   /* request can never fit the HBM budget           */
+
+/* ---- enumerations ------------------------------------------------------------ */
+#define SIFT3D_DTYPE_F32   0   /* input voxels: float32, used as they are        */
+#define SIFT3D_DTYPE_U8    1   /* input voxels: uint8 codes, converted to c/255  */
+
+#define SIFT3D_STORAGE_F32  0  /* pyramid levels stored in float32               */
+#define SIFT3D_STORAGE_F16  1  /* stored in IEEE half, arithmetic in float32     */
+#define SIFT3D_STORAGE_BF16 2  /* stored in bfloat16, arithmetic in float32      */
+
+#define SIFT3D_DESC_BRIEF  1
+#define SIFT3D_DESC_RRIEF  2
+#define SIFT3D_DESC_BOTH   3
+
+#define SIFT3D_LEVEL_GAUSS 0   /* G_s,   s = 0..S+2                              */
+#define SIFT3D_LEVEL_DOG   1   /* D_s = G_s - G_{s+1}, s = 0..S+1                */
+#define SIFT3D_LEVEL_DESC  2   /* G_s pre-blurred for descriptors, s = 1..S      */
+
+#define SIFT3D_SUBMIT_NOCOPY 1 /* submit flag: the caller keeps host_vol valid and
+                                  unchanged until the request finishes; the
+                                  library copies from it asynchronously (pinned
+                                  host memory is read by DMA, no staging copy)  */
+
+#define SIFT3D_MAX_OCTAVES 16
+#define SIFT3D_MAX_SCALES   5  /* scales_per_octave <= 5                         */
+#define SIFT3D_N_PAIRS     64  /* point pairs per descriptor                     */
+
+/* ---- parameters ---------------------------------------------------------------
+ * The Gaussian levels of an octave are G_s, s = 0..S+2, at
+ * sigma_s = sigma0 * 2^(s/S) octave voxels (S = scales_per_octave).  Octave 0
+ * starts with a blur of sqrt(sigma0^2 - sigma_in^2) of the input; G_s is G_{s-1}
+ * blurred by sqrt(sigma_s^2 - sigma_{s-1}^2); octave o+1 starts from the 2x2x2
+ * mean of G_S of octave o.  A 1D pass uses w_k ~ exp(-k^2/2 sigma^2) for
+ * |k| <= ceil(trunc*sigma), normalised to unit sum, with clamp-to-edge borders.
+ * Octaves continue while min(nx,ny,nz) of the octave >= min_octave_dim (and,
+ * if max_octaves > 0, for at most max_octaves octaves).
+ * A voxel v of D_s (s = 1..S, at least `border` voxels from every face) is a
+ * keypoint when
+ *   |sum over the 80 neighbours n of sign(D_s(v) - D(n))| >= sign_sum_min
+ *        (neighbours: 3x3x3 in D_{s-1} and D_{s+1}, 3x3x3 minus v in D_s),
+ *   |D_s(v)| >= contrast_thresh, and
+ *   H' = -polarity * (central-difference Hessian of D_s at v) is positive
+ *   definite with tr(H')^3 * r^2 < (2r+1)^3 * det(H'), r = curvature_r.
+ */
+typedef struct sift3d_params {
+    double   sigma0;             /* 1.6                                        */
+    double   sigma_in;           /* 0.5  nominal blur of the input             */
+    int32_t  scales_per_octave;  /* 3    (S), 1..SIFT3D_MAX_SCALES             */
+    int32_t  min_octave_dim;     /* 16, >= 3                                   */
+    int32_t  max_octaves;        /* 0 = no limit                               */
+    int32_t  sign_sum_min;       /* 80 = strict extremum; 1..80                */
+    int32_t  border;             /* 1, >= 1                                    */
+    int32_t  reserved;           /* 0                                          */
+    double   contrast_thresh;    /* 0.005 (compared in float32 on the device)  */
+    double   curvature_r;        /* 10, > 1                                    */
+    double   trunc;              /* 4.0  filter radius = ceil(trunc * sigma)   */
+    double   desc_blur_sigma;    /* 0.95; 0 = sample G_s without pre-blur     */
+    int32_t  desc_method;        /* 3 (p1 ~ N(0,1), p2 ~ N(p1,1))              */
+    uint64_t pattern_seed;       /* seeds the SplitMix64 pattern generator     */
+    int32_t  storage;            /* SIFT3D_STORAGE_*                           */
+    int32_t  use_graphs;         /* 1 = replay detect as a captured CUDA graph */
+    uint64_t hbm_budget_bytes;   /* serving admission budget (0 = 40 GiB)      */
+    int32_t  max_keypoints;      /* serving: keypoints kept per request (8192) */
+    int32_t  max_inflight;       /* serving: requests on the device at once (4) */
+} sift3d_params;
+
+/* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the
+ * octave voxel centre, (i + 0.5) * 2^octave - 0.5; sigma = sigma_scale * 2^octave
+ * input voxels. */
+typedef struct sift3d_keypoint {
+    float   x, y, z;
+    float   sigma;
+    int32_t ix, iy, iz;          /* position in the octave grid                */
+    int16_t octave, scale;       /* scale s in 1..S                            */
+    int8_t  polarity;            /* +1 DoG peak, -1 valley                     */
+    int8_t  reserved0[3];
+    float   dog;                 /* D_s(ix,iy,iz)                              */
+    int32_t sign_sum;            /* sum of signs over the 80 neighbours        */
+    int32_t reserved1;
+} sift3d_keypoint;
+
+/* Host-side description of the work for one volume size. */
+typedef struct sift3d_plan_info {
+    int32_t  n_octaves;
+    int32_t  n_levels;                          /* S + 3                        */
+    int32_t  dims[SIFT3D_MAX_OCTAVES][3];       /* nx, ny, nz per octave        */
+    int64_t  pitch_y[SIFT3D_MAX_OCTAVES];       /* elements between rows        */
+    int64_t  pitch_z[SIFT3D_MAX_OCTAVES];       /* elements between planes      */
+    double   sigma_level[SIFT3D_MAX_SCALES + 3];/* sigma_s in octave voxels     */
+    double   sigma_initial;                     /* octave-0 initial blur        */
+    double   sigma_increment[SIFT3D_MAX_SCALES + 3]; /* [s-1]: G_{s-1} -> G_s   */
+    int32_t  radius_initial;
+    int32_t  radius_increment[SIFT3D_MAX_SCALES + 3];
+    int32_t  radius_desc;                       /* 0 when desc_blur_sigma == 0  */
+    uint64_t workspace_bytes;                   /* device bytes one detect holds */
+    uint64_t algorithmic_bytes;                 /* byte model of the detect path */
+} sift3d_plan_info;
+
+/* Result of a served request (sift3d_poll).  Arrays are host memory owned by
+ * the library, valid until sift3d_release(ticket). */
+typedef struct sift3d_result {
+    int32_t status;              /* SIFT3D_OK or SIFT3D_ECAPACITY               */
+    int32_t n_keypoints;         /* records in keypoints / brief / rrief        */
+    int32_t n_needed;            /* keypoints detected (> n_keypoints on ECAPACITY) */
+    int32_t nx, ny, nz;
+    const sift3d_keypoint* keypoints;
+    const uint64_t* brief;       /* n_keypoints words, bit k = pair k          */
+    const uint8_t*  rrief;       /* n_keypoints x 64 ranks                      */
+    double  latency_ms;          /* submit -> results ready (host clock)        */
+    double  queue_ms;            /* submit -> admitted to the device            */
+} sift3d_result;
+
+typedef struct sift3d_ctx sift3d_ctx;
+
+/* Fill *out with the defaults listed beside each field above. */
+int sift3d_default_params(sift3d_params* out);
+
+/* Validate params and compute the octave schedule for an nx*ny*nz volume.
+ * Host only; touches no device.  SIFT3D_EINVAL on bad params or dims. */
+int sift3d_plan(const sift3d_params* params, int nx, int ny, int nz,
+                sift3d_plan_info* out);
+
+/* Write the 64 point pairs the descriptors use, as float
+ * out[k*6 + p*3 + c] (pair k, point p in {0,1}, coordinate c = x,y,z), in units
+ * of the keypoint's scale.  Method 3 (Sec. 2.2.3): p1 ~ N(0,1), p2 ~ N(p1,1)
+ * per coordinate, a point with any |coordinate| > 4 redrawn; normals from
+ * SplitMix64 (seeded with pattern_seed) through Box-Muller, one cos branch per
+ * pair of uniforms.  Host only. */
+int sift3d_pattern(const sift3d_params* params, float* out);
+
+/* Create a context.  Validates params (SIFT3D_EINVAL) and stores them; device
+ * memory is allocated lazily by the first call that needs it.  *out receives
+ * the context, or NULL on failure. */
+int sift3d_create(const sift3d_params* params, sift3d_ctx** out);
+
+/* Release a context and all device memory it owns.  NULL is ignored.  Waits
+ * for the context's outstanding work. */
+void sift3d_destroy(sift3d_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none).  Owned by ctx. */
+const char* sift3d_last_error(const sift3d_ctx* ctx);
+
+/* Detect keypoints in one volume (Sec. 2.2.2: Gaussian pyramid, sub-sampling,
+ * DoG, 4D sum-of-signs peaks; plus the contrast and curvature tests).
+ *   dev_vol   device volume of nx*ny*nz voxels of `dtype`, x fastest.
+ *   stream    cudaStream_t the work is ordered on.
+ *   dev_out   device array of `capacity` keypoints, written in the canonical
+ *             order (octave, scale, iz, iy, ix).
+ *   n_out     host int; if non-NULL the call waits for the device and stores
+ *             the number of keypoints detected (which may exceed capacity).  If
+ *             NULL the call returns without waiting; the count is then
+ *             available on the device through sift3d_device_count().
+ * The pyramid stays on the device, owned by ctx, until the next detect on ctx;
+ * sift3d_describe and sift3d_read_level read it.
+ * Errors: SIFT3D_EINVAL (dims, dtype, capacity < 0), SIFT3D_ENOMEM,
+ * SIFT3D_ECUDA, SIFT3D_ECAPACITY (only with n_out: more keypoints than
+ * capacity; the first `capacity` in canonical order were written). */
+int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype,
+                  int nx, int ny, int nz, void* stream,
+                  sift3d_keypoint* dev_out, int capacity, int* n_out);
+
+/* Device pointer to the int that the last detect on ctx writes its keypoint
+ * count to (stream ordered).  NULL before the first detect. */
+const int* sift3d_device_count(const sift3d_ctx* ctx);
+
+/* BRIEF / RRIEF descriptors of keypoints from the last detect on ctx
+ * (Sec. 2.2.3).  For keypoint (octave o, scale s, ix, iy, iz) the level G_s of
+ * octave o is blurred by desc_blur_sigma (clamp), and for each pair k the
+ * values I(c + sigma_s*p1_k) and I(c + sigma_s*p2_k) are read by trilinear
+ * interpolation with coordinates clamped to the octave grid (c = (ix,iy,iz),
+ * sigma_s in octave voxels);  d_k = I(p1_k) - I(p2_k).
+ *   BRIEF: bit k of dev_brief[i] is [d_k > 0].
+ *   RRIEF: dev_rrief[i*64 + k] = #{j : d_j < d_k} + #{j < k : d_j == d_k}.
+ *   n      number of keypoints in dev_kps; -1 = use the device-side count of
+ *          the last detect (min(count, that detect's capacity)), no host wait.
+ *   kind   SIFT3D_DESC_BRIEF / _RRIEF / _BOTH; the unused output may be NULL.
+ * Errors: SIFT3D_EINVAL (no prior detect, bad kind, NULL output), SIFT3D_ECUDA. */
+int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int kind,
+                    uint64_t* dev_brief, uint8_t* dev_rrief, void* stream);
+
+/* Copy one pyramid level of the last detect into a dense float32 device array
+ * dev_dst of dims[octave] voxels (x fastest).  kind = SIFT3D_LEVEL_*.
+ * Errors: SIFT3D_EINVAL (no prior detect, index out of range), SIFT3D_ECUDA. */
+int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index,
+                      float* dev_dst, void* stream);
+
+/* Serving (no counterpart in the paper).  sift3d_submit copies a HOST volume
+ * (the library reads it before returning, unless flags has
+ * SIFT3D_SUBMIT_NOCOPY) into a request and queues it; the
+ * library admits requests to the device while their device memory fits in
+ * hbm_budget_bytes and fewer than max_inflight are on the device, runs detect
+ * then BRIEF+RRIEF describe for each on its own stream, and copies the results
+ * back to host memory.  Requests that overlap in time overlap on the device.
+ *   ticket  receives an id for sift3d_poll / sift3d_release.
+ * Errors: SIFT3D_EINVAL, SIFT3D_EBUDGET (the volume alone exceeds the budget),
+ * SIFT3D_ENOMEM. */
+int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype,
+                  int nx, int ny, int nz, int flags, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds (0 = do not wait) for a request.  Returns
+ * SIFT3D_OK with *out filled, SIFT3D_PENDING if still running, or an error
+ * (SIFT3D_ENOTFOUND for an unknown or released ticket, SIFT3D_ECUDA if its
+ * device work failed).  A result's ECAPACITY is reported in out->status. */
+int sift3d_poll(sift3d_ctx* ctx, uint64_t ticket, int timeout_us, sift3d_result* out);
+
+/* Free the host result of a finished request.  SIFT3D_ENOTFOUND if unknown,
+ * SIFT3D_PENDING if it has not finished (nothing is freed). */
+int sift3d_release(sift3d_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIFT3D_H */

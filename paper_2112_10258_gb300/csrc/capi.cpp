@@ -1,0 +1,635 @@
+// extern "C" entry points of include/sift3d.h and the serving scheduler.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "runtime.hpp"
+
+using namespace sift3d;
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// A workspace for one (shape, dtype, capacity) with its replayable detect.
+struct DetectEntry {
+    Workspace ws;
+    std::unique_ptr<DetectExec> ex[2];   // per input dtype
+    ~DetectEntry() {
+        ex[0].reset();
+        ex[1].reset();
+        free_workspace(&ws);
+    }
+};
+
+using ShapeKey = std::tuple<int, int, int, int>;  // nx, ny, nz, capacity
+
+struct Server;
+
+}  // namespace
+
+struct sift3d_ctx {
+    sift3d_params p{};
+    std::string err;
+    float pattern[SIFT3D_N_PAIRS * 6];
+    int device = -1;
+    std::map<ShapeKey, std::unique_ptr<DetectEntry>> cache;
+    DetectEntry* last = nullptr;
+    std::unique_ptr<Server> server;
+    std::mutex err_mu;
+};
+
+namespace {
+
+int set_err(sift3d_ctx* c, int code, const std::string& msg) {
+    if (c) {
+        std::lock_guard<std::mutex> g(c->err_mu);
+        c->err = msg;
+    }
+    return code;
+}
+
+int ensure_device(sift3d_ctx* c) {
+    if (c->device >= 0) return cudaSetDevice(c->device) == cudaSuccess ? SIFT3D_OK : SIFT3D_ECUDA;
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return set_err(c, SIFT3D_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    c->device = d;
+    return SIFT3D_OK;
+}
+
+int get_entry(sift3d_ctx* c, int nx, int ny, int nz, int dtype, int capacity, DetectEntry** out) {
+    const ShapeKey key{nx, ny, nz, capacity};
+    auto it = c->cache.find(key);
+    if (it == c->cache.end()) {
+        Plan pl;
+        std::string err;
+        int rc = make_plan(c->p, nx, ny, nz, dtype, &pl, &err);
+        if (rc != SIFT3D_OK) return set_err(c, rc, err);
+        auto ent = std::make_unique<DetectEntry>();
+        rc = alloc_workspace(pl, capacity, &ent->ws, &err);
+        if (rc != SIFT3D_OK) return set_err(c, rc, err);
+        it = c->cache.emplace(key, std::move(ent)).first;
+    }
+    DetectEntry* e = it->second.get();
+    if (!e->ex[dtype]) e->ex[dtype] = std::make_unique<DetectExec>();
+    *out = e;
+    return SIFT3D_OK;
+}
+
+int launch(const LaunchSpec& s, void* argp, cudaStream_t st, std::string* err) {
+    void* args[1] = {argp};
+    cudaError_t e = cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
+    if (e != cudaSuccess) {
+        if (err) *err = std::string(s.name) + ": " + cudaGetErrorString(e);
+        return SIFT3D_ECUDA;
+    }
+    return SIFT3D_OK;
+}
+
+// Enqueue detect (no host wait) on an entry's workspace.
+int enqueue_detect(DetectEntry* ent, const void* vol, int dtype, sift3d_keypoint* out, bool graphs,
+                   cudaStream_t st, std::string* err) {
+    if (ent->ws.plan.nO == 0) {
+        cudaError_t e = cudaMemsetAsync(ent->ws.count_out, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ent->ws.count, 0, sizeof(int), st);
+        if (e != cudaSuccess) {
+            if (err) *err = cudaGetErrorString(e);
+            return SIFT3D_ECUDA;
+        }
+        return SIFT3D_OK;
+    }
+    DetectCall call{vol, dtype, out, ent->ws.capacity};
+    return run_detect(ent->ws, *ent->ex[dtype], call, graphs, st, err);
+}
+
+int enqueue_describe(const DetectEntry* ent, const float* pattern, const sift3d_keypoint* kps, int n, int kind,
+                     uint64_t* brief, uint8_t* rrief, cudaStream_t st, std::string* err) {
+    DescribeArgs a = make_describe_args(ent->ws, pattern);
+    a.kps = kps;
+    a.n = n;
+    a.n_dev = ent->ws.count_out;
+    a.n_cap = ent->ws.capacity;
+    a.brief = (kind & SIFT3D_DESC_BRIEF) ? brief : nullptr;
+    a.rrief = (kind & SIFT3D_DESC_RRIEF) ? rrief : nullptr;
+    const int n_max = n >= 0 ? n : ent->ws.capacity;
+    if (n_max == 0 || ent->ws.plan.nO == 0) return SIFT3D_OK;
+    LaunchSpec s = describe_spec(ent->ws.plan.p.storage, a, n_max);
+    return launch(s, &a, st, err);
+}
+
+// ----------------------------------------------------------------------------
+// Serving: a worker thread admits queued requests while their device bytes fit
+// the HBM budget and a slot is free, runs each on its own stream (so requests
+// overlap on the device), and retires them when their completion event fires.
+// ----------------------------------------------------------------------------
+struct ServeBuffers {            // device + pinned buffers for one (shape, dtype)
+    std::unique_ptr<DetectEntry> ent;
+    int dtype = 0;
+    void* d_in = nullptr;
+    size_t in_bytes = 0;
+    sift3d_keypoint* d_kps = nullptr;
+    uint64_t* d_brief = nullptr;
+    uint8_t* d_rrief = nullptr;
+    void* h_in = nullptr;        // pinned staging of the input
+    sift3d_keypoint* h_kps = nullptr;
+    uint64_t* h_brief = nullptr;
+    uint8_t* h_rrief = nullptr;
+    int* h_count = nullptr;
+    size_t bytes = 0;            // device bytes held
+    ~ServeBuffers() {
+        cudaFree(d_in);
+        cudaFree(d_kps);
+        cudaFree(d_brief);
+        cudaFree(d_rrief);
+        cudaFreeHost(h_in);
+        cudaFreeHost(h_kps);
+        cudaFreeHost(h_brief);
+        cudaFreeHost(h_rrief);
+        cudaFreeHost(h_count);
+    }
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    int dtype = 0, nx = 0, ny = 0, nz = 0, flags = 0;
+    const void* user_in = nullptr;       // NOCOPY
+    std::vector<uint8_t> host_copy;      // default: copied at submit
+    enum State { QUEUED, RUNNING, DONE, FAILED } state = QUEUED;
+    int status = SIFT3D_OK;
+    std::string err;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::unique_ptr<ServeBuffers> buf;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int n_kps = 0, n_needed = 0;
+    std::vector<sift3d_keypoint> kps;
+    std::vector<uint64_t> brief;
+    std::vector<uint8_t> rrief;
+};
+
+struct Server {
+    sift3d_ctx* ctx;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> running;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::multimap<std::tuple<int, int, int, int>, std::unique_ptr<ServeBuffers>> pool;  // idle buffers
+    std::vector<cudaStream_t> streams;   // free streams
+    uint64_t next_ticket = 1;
+    uint64_t budget = 0, used = 0, pooled = 0;
+    bool stop = false;
+    std::thread th;
+
+    explicit Server(sift3d_ctx* c) : ctx(c) {
+        budget = c->p.hbm_budget_bytes ? c->p.hbm_budget_bytes : (40ull << 30);
+        th = std::thread([this] { loop(); });
+    }
+    ~Server() {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            stop = true;
+        }
+        cv_work.notify_all();
+        th.join();
+        for (Request* r : running) {
+            cudaEventSynchronize(r->done);
+            cudaEventDestroy(r->done);
+        }
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+        pool.clear();
+    }
+
+    uint64_t request_bytes(int nx, int ny, int nz, int dtype, std::string* err, int* rc) {
+        Plan pl;
+        *rc = make_plan(ctx->p, nx, ny, nz, dtype, &pl, err);
+        if (*rc != SIFT3D_OK) return 0;
+        const size_t cap = (size_t)std::max(ctx->p.max_keypoints, 1);
+        return pl.bytes + cap * (sizeof(sift3d_keypoint) * 2 + 8 + 64) + (size_t)nx * ny * nz * 4 + (1 << 20);
+    }
+
+    std::unique_ptr<ServeBuffers> take_buffers(const Request& r, std::string* err, int* rc) {
+        const auto key = std::make_tuple(r.nx, r.ny, r.nz, r.dtype);
+        auto it = pool.find(key);
+        if (it != pool.end()) {
+            auto b = std::move(it->second);
+            pool.erase(it);
+            pooled -= b->bytes;
+            return b;
+        }
+        auto b = std::make_unique<ServeBuffers>();
+        b->dtype = r.dtype;
+        const int cap = std::max(ctx->p.max_keypoints, 1);
+        Plan pl;
+        *rc = make_plan(ctx->p, r.nx, r.ny, r.nz, r.dtype, &pl, err);
+        if (*rc != SIFT3D_OK) return nullptr;
+        b->ent = std::make_unique<DetectEntry>();
+        *rc = alloc_workspace(pl, cap, &b->ent->ws, err);
+        if (*rc != SIFT3D_OK) return nullptr;
+        b->ent->ex[r.dtype] = std::make_unique<DetectExec>();
+        b->in_bytes = (size_t)r.nx * r.ny * r.nz * (r.dtype == SIFT3D_DTYPE_U8 ? 1 : 4);
+        cudaError_t e = cudaMalloc(&b->d_in, b->in_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_kps, (size_t)cap * sizeof(sift3d_keypoint));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_brief, (size_t)cap * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_rrief, (size_t)cap * 64);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_in, b->in_bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_kps, (size_t)cap * sizeof(sift3d_keypoint));
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_brief, (size_t)cap * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_rrief, (size_t)cap * 64);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_count, 2 * sizeof(int));
+        if (e != cudaSuccess) {
+            *err = std::string("serving buffers: ") + cudaGetErrorString(e);
+            *rc = e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        b->bytes = b->ent->ws.bytes + b->in_bytes + (size_t)cap * (sizeof(sift3d_keypoint) + 8 + 64);
+        return b;
+    }
+
+    // Free idle pooled buffers until `need` more bytes fit in the budget.
+    void evict_for(uint64_t need) {
+        while (used + pooled + need > budget && !pool.empty()) {
+            auto it = pool.begin();
+            pooled -= it->second->bytes;
+            pool.erase(it);   // synchronising cudaFree: only on shape churn
+        }
+    }
+
+    int admit(Request* r) {
+        std::string err;
+        int rc = SIFT3D_OK;
+        const uint64_t est = request_bytes(r->nx, r->ny, r->nz, r->dtype, &err, &rc);
+        evict_for(est);
+        r->buf = take_buffers(*r, &err, &rc);
+        if (!r->buf) {
+            r->status = rc == SIFT3D_OK ? SIFT3D_ECUDA : rc;
+            r->err = err;
+            r->t_admit = r->t_done = now_ms();
+            r->state = Request::FAILED;
+            return r->status;
+        }
+        used += r->buf->bytes;
+        if (streams.empty()) {
+            cudaStream_t s;
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            streams.push_back(s);
+        }
+        r->stream = streams.back();
+        streams.pop_back();
+        cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+        ServeBuffers& b = *r->buf;
+        const void* src = r->user_in;
+        if (!(r->flags & SIFT3D_SUBMIT_NOCOPY)) {
+            memcpy(b.h_in, r->host_copy.data(), b.in_bytes);
+            src = b.h_in;
+        }
+        cudaError_t e = cudaMemcpyAsync(b.d_in, src, b.in_bytes, cudaMemcpyHostToDevice, r->stream);
+        if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
+        if (rc == SIFT3D_OK)
+            rc = enqueue_detect(b.ent.get(), b.d_in, r->dtype, b.d_kps, ctx->p.use_graphs != 0, r->stream, &err);
+        if (rc == SIFT3D_OK)
+            rc = enqueue_describe(b.ent.get(), ctx->pattern, b.d_kps, -1, SIFT3D_DESC_BOTH, b.d_brief, b.d_rrief,
+                                  r->stream, &err);
+        const int cap = b.ent->ws.capacity;
+        if (rc == SIFT3D_OK) {
+            e = cudaMemcpyAsync(b.h_count, b.ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, r->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b.h_kps, b.d_kps, (size_t)cap * sizeof(sift3d_keypoint), cudaMemcpyDeviceToHost,
+                                    r->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b.h_brief, b.d_brief, (size_t)cap * 8, cudaMemcpyDeviceToHost, r->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b.h_rrief, b.d_rrief, (size_t)cap * 64, cudaMemcpyDeviceToHost, r->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(r->done, r->stream);
+            if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
+        }
+        r->t_admit = now_ms();
+        if (rc != SIFT3D_OK) {
+            r->status = rc;
+            r->err = err;
+        }
+        r->state = Request::RUNNING;
+        running.push_back(r);
+        return rc;
+    }
+
+    void retire(Request* r) {
+        ServeBuffers& b = *r->buf;
+        if (r->status == SIFT3D_OK) {
+            const int total = *b.h_count;
+            const int cap = b.ent->ws.capacity;
+            r->n_needed = total;
+            r->n_kps = std::min(total, cap);
+            r->kps.assign(b.h_kps, b.h_kps + r->n_kps);
+            r->brief.assign(b.h_brief, b.h_brief + r->n_kps);
+            r->rrief.assign(b.h_rrief, b.h_rrief + (size_t)r->n_kps * 64);
+            if (total > cap) r->status = SIFT3D_ECAPACITY;
+        }
+        cudaEventDestroy(r->done);
+        r->done = nullptr;
+        streams.push_back(r->stream);
+        r->stream = nullptr;
+        used -= b.bytes;
+        pooled += b.bytes;
+        pool.emplace(std::make_tuple(r->nx, r->ny, r->nz, r->dtype), std::move(r->buf));
+        r->host_copy.clear();
+        r->host_copy.shrink_to_fit();
+        r->t_done = now_ms();
+        r->state = (r->status == SIFT3D_OK || r->status == SIFT3D_ECAPACITY) ? Request::DONE : Request::FAILED;
+    }
+
+    void loop() {
+        cudaSetDevice(ctx->device);
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            bool progressed = false;
+            for (size_t i = 0; i < running.size();) {
+                Request* r = running[i];
+                const cudaError_t q = r->status == SIFT3D_OK ? cudaEventQuery(r->done) : cudaSuccess;
+                if (q == cudaErrorNotReady) {
+                    ++i;
+                    continue;
+                }
+                if (q != cudaSuccess && r->status == SIFT3D_OK) {
+                    r->status = SIFT3D_ECUDA;
+                    r->err = cudaGetErrorString(q);
+                }
+                if (r->status != SIFT3D_OK && r->done) cudaEventSynchronize(r->done);
+                retire(r);
+                running.erase(running.begin() + i);
+                progressed = true;
+            }
+            while (!queue.empty() && (int)running.size() < ctx->p.max_inflight) {
+                Request* r = queue.front();
+                std::string err;
+                int rc = SIFT3D_OK;
+                const uint64_t est = request_bytes(r->nx, r->ny, r->nz, r->dtype, &err, &rc);
+                if (used + est > budget && !running.empty()) break;   // wait for memory to free up
+                queue.pop_front();
+                admit(r);
+                progressed = true;
+            }
+            if (progressed) cv_done.notify_all();
+            if (stop && queue.empty() && running.empty()) break;
+            if (running.empty() && queue.empty()) {
+                cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+            } else if (!progressed) {
+                cv_work.wait_for(lk, std::chrono::microseconds(20));
+            }
+        }
+    }
+};
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int sift3d_default_params(sift3d_params* out) {
+    if (!out) return SIFT3D_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->sigma0 = 1.6;
+    out->sigma_in = 0.5;
+    out->scales_per_octave = 3;
+    out->min_octave_dim = 16;
+    out->max_octaves = 0;
+    out->sign_sum_min = 80;
+    out->border = 1;
+    out->contrast_thresh = 0.005;
+    out->curvature_r = 10.0;
+    out->trunc = 4.0;
+    out->desc_blur_sigma = 0.95;
+    out->desc_method = 3;
+    out->pattern_seed = 0x5EED5EEDull;
+    out->storage = SIFT3D_STORAGE_F32;
+    out->use_graphs = 1;
+    out->hbm_budget_bytes = 40ull << 30;
+    out->max_keypoints = 8192;
+    out->max_inflight = 4;
+    return SIFT3D_OK;
+}
+
+int sift3d_plan(const sift3d_params* params, int nx, int ny, int nz, sift3d_plan_info* out) {
+    if (!params || !out) return SIFT3D_EINVAL;
+    Plan pl;
+    int rc = make_plan(*params, nx, ny, nz, SIFT3D_DTYPE_F32, &pl, nullptr);
+    if (rc != SIFT3D_OK) return rc;
+    fill_plan_info(pl, out);
+    return SIFT3D_OK;
+}
+
+int sift3d_pattern(const sift3d_params* params, float* out) {
+    if (!params || !out) return SIFT3D_EINVAL;
+    make_pattern(*params, out);
+    return SIFT3D_OK;
+}
+
+int sift3d_create(const sift3d_params* params, sift3d_ctx** out) {
+    if (!out) return SIFT3D_EINVAL;
+    *out = nullptr;
+    if (!params) return SIFT3D_EINVAL;
+    std::string err;
+    const int rc = validate_params(*params, &err);
+    if (rc != SIFT3D_OK) return rc;
+    auto* c = new (std::nothrow) sift3d_ctx();
+    if (!c) return SIFT3D_ENOMEM;
+    c->p = *params;
+    make_pattern(c->p, c->pattern);
+    *out = c;
+    return SIFT3D_OK;
+}
+
+void sift3d_destroy(sift3d_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->device >= 0) cudaSetDevice(ctx->device);
+    ctx->server.reset();
+    if (ctx->device >= 0) cudaDeviceSynchronize();
+    ctx->cache.clear();
+    delete ctx;
+}
+
+const char* sift3d_last_error(const sift3d_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int ny, int nz, void* stream,
+                  sift3d_keypoint* dev_out, int capacity, int* n_out) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!dev_vol) return set_err(ctx, SIFT3D_EINVAL, "dev_vol is NULL");
+    if (dtype != SIFT3D_DTYPE_F32 && dtype != SIFT3D_DTYPE_U8) return set_err(ctx, SIFT3D_EINVAL, "bad dtype");
+    if (capacity < 0 || capacity > (1 << 20)) return set_err(ctx, SIFT3D_EINVAL, "capacity must be in 0..2^20");
+    if (capacity > 0 && !dev_out) return set_err(ctx, SIFT3D_EINVAL, "dev_out is NULL");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4095 || ny > 4095 || nz > 4095)
+        return set_err(ctx, SIFT3D_EINVAL, "each dimension must be in 1..4095");
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    DetectEntry* ent = nullptr;
+    rc = get_entry(ctx, nx, ny, nz, dtype, capacity, &ent);
+    if (rc != SIFT3D_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::string err;
+    rc = enqueue_detect(ent, dev_vol, dtype, dev_out, ctx->p.use_graphs != 0, st, &err);
+    if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
+    ctx->last = ent;
+    if (n_out) {
+        int h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("detect: ") + cudaGetErrorString(e));
+        if (h < 0) return set_err(ctx, SIFT3D_ECUDA, "keypoint sort had no scratch space");
+        *n_out = h;
+        if (h > capacity) return set_err(ctx, SIFT3D_ECAPACITY, "more keypoints than capacity");
+    }
+    return SIFT3D_OK;
+}
+
+const int* sift3d_device_count(const sift3d_ctx* ctx) {
+    return (ctx && ctx->last) ? ctx->last->ws.count_out : nullptr;
+}
+
+int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int kind, uint64_t* dev_brief,
+                    uint8_t* dev_rrief, void* stream) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->last) return set_err(ctx, SIFT3D_EINVAL, "describe needs a prior detect");
+    if (kind < SIFT3D_DESC_BRIEF || kind > SIFT3D_DESC_BOTH) return set_err(ctx, SIFT3D_EINVAL, "bad kind");
+    if (((kind & SIFT3D_DESC_BRIEF) && !dev_brief) || ((kind & SIFT3D_DESC_RRIEF) && !dev_rrief))
+        return set_err(ctx, SIFT3D_EINVAL, "descriptor output is NULL");
+    if (n < -1) return set_err(ctx, SIFT3D_EINVAL, "n must be >= -1");
+    if (n != 0 && !dev_kps) return set_err(ctx, SIFT3D_EINVAL, "dev_kps is NULL");
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    std::string err;
+    rc = enqueue_describe(ctx->last, ctx->pattern, dev_kps, n, kind, dev_brief, dev_rrief,
+                          static_cast<cudaStream_t>(stream), &err);
+    return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
+}
+
+int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index, float* dev_dst, void* stream) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->last) return set_err(ctx, SIFT3D_EINVAL, "read_level needs a prior detect");
+    if (!dev_dst) return set_err(ctx, SIFT3D_EINVAL, "dev_dst is NULL");
+    const Workspace& ws = ctx->last->ws;
+    const Plan& pl = ws.plan;
+    if (octave < 0 || octave >= pl.nO) return set_err(ctx, SIFT3D_EINVAL, "octave out of range");
+    const void* src = nullptr;
+    if (kind == SIFT3D_LEVEL_GAUSS && index >= 0 && index < pl.L) src = ws.G(octave, index);
+    else if (kind == SIFT3D_LEVEL_DOG && index >= 0 && index < pl.nD) src = ws.D(octave, index);
+    else if (kind == SIFT3D_LEVEL_DESC && index >= 1 && index <= pl.S) src = ws.B(octave, index);
+    if (!src) return set_err(ctx, SIFT3D_EINVAL, "level kind/index out of range");
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    ReadLevelArgs a{};
+    a.src = src;
+    a.py = pl.oct[octave].py;
+    a.pz = pl.oct[octave].pz;
+    a.nx = pl.oct[octave].nx;
+    a.ny = pl.oct[octave].ny;
+    a.nz = pl.oct[octave].nz;
+    a.dst = dev_dst;
+    std::string err;
+    rc = launch(read_level_spec(pl.p.storage, a), &a, static_cast<cudaStream_t>(stream), &err);
+    return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
+}
+
+int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype, int nx, int ny, int nz, int flags,
+                  uint64_t* ticket) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!host_vol || !ticket) return set_err(ctx, SIFT3D_EINVAL, "host_vol and ticket must be non-NULL");
+    if (dtype != SIFT3D_DTYPE_F32 && dtype != SIFT3D_DTYPE_U8) return set_err(ctx, SIFT3D_EINVAL, "bad dtype");
+    if (flags & ~SIFT3D_SUBMIT_NOCOPY) return set_err(ctx, SIFT3D_EINVAL, "unknown flags");
+    Plan pl;
+    std::string err;
+    int rc = make_plan(ctx->p, nx, ny, nz, dtype, &pl, &err);
+    if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
+    rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    if (!ctx->server) ctx->server = std::make_unique<Server>(ctx);
+    Server& sv = *ctx->server;
+    const uint64_t need = sv.request_bytes(nx, ny, nz, dtype, &err, &rc);
+    if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
+    if (need > sv.budget) return set_err(ctx, SIFT3D_EBUDGET, "volume alone exceeds hbm_budget_bytes");
+    auto r = std::make_unique<Request>();
+    r->dtype = dtype;
+    r->nx = nx;
+    r->ny = ny;
+    r->nz = nz;
+    r->flags = flags;
+    r->t_submit = now_ms();
+    const size_t bytes = (size_t)nx * ny * nz * (dtype == SIFT3D_DTYPE_U8 ? 1 : 4);
+    if (flags & SIFT3D_SUBMIT_NOCOPY) {
+        r->user_in = host_vol;
+    } else {
+        try {
+            r->host_copy.assign(static_cast<const uint8_t*>(host_vol), static_cast<const uint8_t*>(host_vol) + bytes);
+        } catch (...) {
+            return set_err(ctx, SIFT3D_ENOMEM, "host copy of the volume failed");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> g(sv.mu);
+        r->ticket = sv.next_ticket++;
+        *ticket = r->ticket;
+        sv.queue.push_back(r.get());
+        sv.reqs.emplace(r->ticket, std::move(r));
+    }
+    sv.cv_work.notify_all();
+    return SIFT3D_OK;
+}
+
+int sift3d_poll(sift3d_ctx* ctx, uint64_t ticket, int timeout_us, sift3d_result* out) {
+    if (!ctx || !out) return SIFT3D_EINVAL;
+    if (!ctx->server) return SIFT3D_ENOTFOUND;
+    Server& sv = *ctx->server;
+    std::unique_lock<std::mutex> lk(sv.mu);
+    auto it = sv.reqs.find(ticket);
+    if (it == sv.reqs.end()) return SIFT3D_ENOTFOUND;
+    Request* r = it->second.get();
+    auto finished = [&] { return r->state == Request::DONE || r->state == Request::FAILED; };
+    if (!finished() && timeout_us > 0)
+        sv.cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), finished);
+    if (!finished()) return SIFT3D_PENDING;
+    memset(out, 0, sizeof(*out));
+    out->status = r->status;
+    out->nx = r->nx;
+    out->ny = r->ny;
+    out->nz = r->nz;
+    out->latency_ms = r->t_done - r->t_submit;
+    out->queue_ms = r->t_admit - r->t_submit;
+    if (r->state == Request::FAILED) {
+        lk.unlock();
+        return set_err(ctx, r->status == SIFT3D_OK ? SIFT3D_ECUDA : r->status, r->err);
+    }
+    out->n_keypoints = r->n_kps;
+    out->n_needed = r->n_needed;
+    out->keypoints = r->kps.data();
+    out->brief = r->brief.data();
+    out->rrief = r->rrief.data();
+    return SIFT3D_OK;
+}
+
+int sift3d_release(sift3d_ctx* ctx, uint64_t ticket) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->server) return SIFT3D_ENOTFOUND;
+    Server& sv = *ctx->server;
+    std::lock_guard<std::mutex> g(sv.mu);
+    auto it = sv.reqs.find(ticket);
+    if (it == sv.reqs.end()) return SIFT3D_ENOTFOUND;
+    const auto st = it->second->state;
+    if (st != Request::DONE && st != Request::FAILED) return SIFT3D_PENDING;
+    sv.reqs.erase(it);
+    return SIFT3D_OK;
+}
+
+}  // extern "C"

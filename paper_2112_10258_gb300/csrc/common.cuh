@@ -1,0 +1,136 @@
+// Internal declarations shared by the sm_103a kernels and the host runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <utility>
+
+#include "sift3d.h"
+
+namespace sift3d {
+
+constexpr int kMaxRadius = 16;     // largest 1D filter radius with a kernel instance
+constexpr int kMaxLevels = SIFT3D_MAX_SCALES + 3;
+constexpr int kMaxDogs = SIFT3D_MAX_SCALES + 2;
+
+// ---- storage types: levels may be stored narrower than the float32 arithmetic
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(uint8_t v) { return (float)v; }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// Taps of a symmetric 1D Gaussian: w[0] is the centre, w[k] the weight at +-k.
+struct Taps {
+    float w[kMaxRadius + 1];
+};
+
+// ---- conv_xy: y pass then x pass of one plane tile, result (float) to dst -------
+// The source plane is read with clamp-to-edge in x and y.  With `sub` set, the
+// source is the previous octave's level S and each source voxel is the 2x2x2
+// mean at (2x.., 2y.., 2z..) (the octave sub-sampling, Sec. 2.2.2); the tile's
+// own voxels of that mean are also written to `base_out` (G_0 of the octave).
+struct ConvXYArgs {
+    const void* src;          // element type per kernel instance
+    int64_t src_py, src_pz;   // source pitches (elements)
+    float src_scale;          // multiplies each source value (1/255 for uint8)
+    float* dst;               // intermediate (float32), level pitches
+    int64_t py, pz;           // pitches of dst / base_out
+    int nx, ny, nz;           // dims of this octave
+    void* base_out;           // sub mode: G_0 of this octave (storage type), else null
+    int* zero_count;          // if set, block (0,0,0) zeroes this counter first
+    Taps taps;
+};
+
+// ---- conv_z: z pass over columns, epilogue writes G_s and the DoG -------------
+struct ConvZArgs {
+    const float* src;         // intermediate from conv_xy
+    void* dst;                // G_s (storage type)
+    const void* prev;         // G_{s-1} for the DoG, or null
+    void* dog;                // D_{s-1} = G_{s-1} - G_s, or null
+    int64_t py, pz;           // shared pitches
+    int nx, ny, nz;
+    Taps taps;
+};
+
+// ---- peak detection + compaction --------------------------------------------
+struct PeakArgs {
+    const void* dog[kMaxDogs];   // D_0..D_{S+1} of the octave (storage type)
+    int64_t py, pz;
+    int nx, ny, nz;
+    int octave, n_scales, border, sign_sum_min;
+    float contrast, curv_k1, curv_k2;   // (2r+1)^3 and r^2
+    float sigma_level[kMaxLevels];      // sigma_s in octave voxels
+    sift3d_keypoint* out;               // staging records
+    int* count;                         // running total (all octaves)
+    int capacity;
+};
+
+// ---- canonical sort of the staging records into the caller's array --------
+struct SortArgs {
+    const sift3d_keypoint* staging;
+    sift3d_keypoint* out;
+    const int* count;
+    int* count_out;             // total detected (may exceed capacity)
+    int capacity;
+    unsigned long long* scratch_keys;  // >= next_pow2(capacity) entries, for large n
+    int scratch_len;
+};
+
+// ---- descriptors --------------------------------------------------------------
+struct DescLevel {
+    const void* ptr;           // pre-blurred G_s (storage type)
+    int64_t py, pz;
+    int nx, ny, nz;
+    float sigma;               // sigma_s in octave voxels
+};
+
+struct DescribeArgs {
+    const sift3d_keypoint* kps;
+    int n;                     // >= 0: count; < 0: read *n_dev, clamp to n_cap
+    const int* n_dev;
+    int n_cap;
+    int n_scales;
+    int n_octaves;
+    DescLevel lv[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES];
+    float pattern[SIFT3D_N_PAIRS * 6];
+    uint64_t* brief;
+    uint8_t* rrief;
+};
+
+struct ReadLevelArgs {
+    const void* src;
+    int64_t py, pz;
+    int nx, ny, nz;
+    float* dst;
+};
+
+// A kernel launch with its single by-value argument struct, usable both for a
+// direct launch and as a CUDA graph kernel node.
+struct LaunchSpec {
+    const void* func = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+    const char* name = "";
+};
+
+// Launch builders (one per kernel family).  `storage` is SIFT3D_STORAGE_*,
+// `src_kind` for conv_xy is 0 = float32, 1 = uint8, 2 = storage type.
+LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const ConvXYArgs& a);
+LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a);
+LaunchSpec peak_spec(int storage, const PeakArgs& a);
+LaunchSpec sort_spec(const SortArgs& a);
+LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
+LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
+
+}  // namespace sift3d

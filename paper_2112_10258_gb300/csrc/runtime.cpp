@@ -1,0 +1,494 @@
+// Host runtime: parameter validation, the octave plan (Sec. 2.2.2 scale
+// schedule), the method-3 point-pair pattern (Sec. 2.2.3), device workspaces,
+// the detect DAG and its execution.
+#include "runtime.hpp"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+namespace sift3d {
+
+namespace {
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int radius_of(double sigma, double trunc) { return (int)std::ceil(trunc * sigma); }
+
+// Sampled Gaussian on |k| <= R, normalised to unit sum in double, then float.
+Taps make_taps(double sigma, int R) {
+    Taps t{};
+    double w[kMaxRadius + 1];
+    double sum = 0.0;
+    for (int k = 0; k <= R; ++k) {
+        w[k] = std::exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        sum += k == 0 ? w[k] : 2.0 * w[k];
+    }
+    for (int k = 0; k <= R; ++k) t.w[k] = (float)(w[k] / sum);
+    return t;
+}
+
+int fail(std::string* err, const char* msg) {
+    if (err) *err = msg;
+    return SIFT3D_EINVAL;
+}
+
+}  // namespace
+
+int validate_params(const sift3d_params& p, std::string* err) {
+    if (!(p.sigma0 > 0.0) || !(p.sigma_in >= 0.0) || !(p.sigma0 > p.sigma_in))
+        return fail(err, "need sigma0 > sigma_in >= 0");
+    if (p.scales_per_octave < 1 || p.scales_per_octave > SIFT3D_MAX_SCALES)
+        return fail(err, "scales_per_octave must be in 1..5");
+    if (p.border < 1) return fail(err, "border must be >= 1");
+    if (p.min_octave_dim < 3 || p.min_octave_dim < 2 * p.border + 1)
+        return fail(err, "min_octave_dim must be >= max(3, 2*border+1)");
+    if (p.max_octaves < 0 || p.max_octaves > SIFT3D_MAX_OCTAVES) return fail(err, "max_octaves must be in 0..16");
+    if (p.sign_sum_min < 1 || p.sign_sum_min > 80) return fail(err, "sign_sum_min must be in 1..80");
+    if (!(p.contrast_thresh >= 0.0) || !std::isfinite(p.contrast_thresh))
+        return fail(err, "contrast_thresh must be finite and >= 0");
+    if (!(p.curvature_r >= 1.0) || !std::isfinite(p.curvature_r)) return fail(err, "curvature_r must be >= 1");
+    if (!(p.trunc > 0.0) || !(p.trunc <= 10.0)) return fail(err, "trunc must be in (0, 10]");
+    if (!(p.desc_blur_sigma >= 0.0) || !std::isfinite(p.desc_blur_sigma))
+        return fail(err, "desc_blur_sigma must be finite and >= 0");
+    if (p.desc_method != 3) return fail(err, "only desc_method 3 is implemented");
+    if (p.storage < SIFT3D_STORAGE_F32 || p.storage > SIFT3D_STORAGE_BF16) return fail(err, "bad storage");
+    if (p.max_keypoints < 0 || p.max_keypoints > (1 << 20)) return fail(err, "max_keypoints must be in 0..2^20");
+    if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
+    // filter radii of the schedule
+    const int S = p.scales_per_octave;
+    double sig[kMaxLevels];
+    for (int s = 0; s < S + 3; ++s) sig[s] = p.sigma0 * std::pow(2.0, (double)s / S);
+    const double s_init = std::sqrt(p.sigma0 * p.sigma0 - p.sigma_in * p.sigma_in);
+    int rmax = radius_of(s_init, p.trunc);
+    for (int s = 1; s < S + 3; ++s) {
+        const double inc = std::sqrt(sig[s] * sig[s] - sig[s - 1] * sig[s - 1]);
+        rmax = std::max(rmax, radius_of(inc, p.trunc));
+    }
+    if (p.desc_blur_sigma > 0.0) rmax = std::max(rmax, radius_of(p.desc_blur_sigma, p.trunc));
+    if (rmax > kMaxRadius) return fail(err, "a filter radius ceil(trunc*sigma) exceeds 16");
+    return SIFT3D_OK;
+}
+
+int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan* out, std::string* err) {
+    int rc = validate_params(p, err);
+    if (rc != SIFT3D_OK) return rc;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4095 || ny > 4095 || nz > 4095)
+        return fail(err, "each dimension must be in 1..4095");
+    Plan& pl = *out;
+    pl = Plan{};
+    pl.p = p;
+    pl.nx = nx;
+    pl.ny = ny;
+    pl.nz = nz;
+    pl.S = p.scales_per_octave;
+    pl.L = pl.S + 3;
+    pl.nD = pl.S + 2;
+    pl.elem = p.storage == SIFT3D_STORAGE_F32 ? 4 : 2;
+    for (int s = 0; s < pl.L; ++s) pl.sig_level[s] = p.sigma0 * std::pow(2.0, (double)s / pl.S);
+    pl.sig_init = std::sqrt(p.sigma0 * p.sigma0 - p.sigma_in * p.sigma_in);
+    pl.r_init = radius_of(pl.sig_init, p.trunc);
+    pl.t_init = make_taps(pl.sig_init, pl.r_init);
+    for (int s = 1; s < pl.L; ++s) {
+        pl.sig_inc[s - 1] = std::sqrt(pl.sig_level[s] * pl.sig_level[s] - pl.sig_level[s - 1] * pl.sig_level[s - 1]);
+        pl.r_inc[s - 1] = radius_of(pl.sig_inc[s - 1], p.trunc);
+        pl.t_inc[s - 1] = make_taps(pl.sig_inc[s - 1], pl.r_inc[s - 1]);
+    }
+    pl.sig_desc = p.desc_blur_sigma;
+    pl.r_desc = p.desc_blur_sigma > 0.0 ? radius_of(p.desc_blur_sigma, p.trunc) : 0;
+    if (pl.r_desc > 0) pl.t_desc = make_taps(pl.sig_desc, pl.r_desc);
+
+    int cx = nx, cy = ny, cz = nz;
+    while (std::min(cx, std::min(cy, cz)) >= p.min_octave_dim &&
+           (p.max_octaves <= 0 || pl.nO < p.max_octaves) && pl.nO < SIFT3D_MAX_OCTAVES) {
+        OctaveGeom& g = pl.oct[pl.nO++];
+        g.nx = cx;
+        g.ny = cy;
+        g.nz = cz;
+        g.py = (int64_t)round_up((size_t)cx, 8);
+        g.pz = g.py * cy;
+        cx /= 2;
+        cy /= 2;
+        cz /= 2;
+    }
+    if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
+
+    size_t off = 0;
+    for (int o = 0; o < pl.nO; ++o) {
+        const size_t lvl = round_up((size_t)(pl.oct[o].pz * pl.oct[o].nz) * pl.elem, 256);
+        const size_t tmp = round_up((size_t)(pl.oct[o].pz * pl.oct[o].nz) * 4, 256);
+        for (int s = 0; s < pl.L; ++s) { pl.off_G[o][s] = off; off += lvl; }
+        for (int s = 0; s < pl.nD; ++s) { pl.off_D[o][s] = off; off += lvl; }
+        if (pl.r_desc > 0)
+            for (int s = 0; s < pl.S; ++s) { pl.off_B[o][s] = off; off += lvl; }
+        pl.off_T[o] = off;
+        off += tmp;
+        if (pl.r_desc > 0)
+            for (int s = 0; s < pl.S; ++s) { pl.off_TB[o][s] = off; off += tmp; }
+    }
+    pl.bytes = off;
+
+    // Byte model of the pyramid + DoG + peak path per volume: per octave
+    // 1 read of the base, L-1 writes of G_1.., L-2 re-reads of G_1.. as filter
+    // input, L-1 writes and L-1 reads of D, 1 read of G_S, 1/8 write of the next
+    // base; octave 0 also writes G_0 and reads the input at its own width.
+    const double per_octave = 4.0 * pl.L - 2.875;
+    double model = 0.0;
+    for (int o = 0; o < pl.nO; ++o) model += per_octave * (double)pl.oct[o].voxels() * (double)pl.elem;
+    if (pl.nO > 0) {
+        const double in_elem = in_dtype == SIFT3D_DTYPE_U8 ? 1.0 : 4.0;
+        const double n0 = (double)pl.oct[0].voxels();
+        model += n0 * (double)pl.elem;                  // octave 0 writes G_0
+        model += n0 * (in_elem - (double)pl.elem);      // its base read is the input
+    }
+    pl.algo_bytes = (uint64_t)std::llround(model);
+    return SIFT3D_OK;
+}
+
+void fill_plan_info(const Plan& pl, sift3d_plan_info* info) {
+    memset(info, 0, sizeof(*info));
+    info->n_octaves = pl.nO;
+    info->n_levels = pl.L;
+    for (int o = 0; o < pl.nO; ++o) {
+        info->dims[o][0] = pl.oct[o].nx;
+        info->dims[o][1] = pl.oct[o].ny;
+        info->dims[o][2] = pl.oct[o].nz;
+        info->pitch_y[o] = pl.oct[o].py;
+        info->pitch_z[o] = pl.oct[o].pz;
+    }
+    for (int s = 0; s < pl.L; ++s) info->sigma_level[s] = pl.sig_level[s];
+    info->sigma_initial = pl.sig_init;
+    info->radius_initial = pl.r_init;
+    for (int s = 0; s + 1 < pl.L; ++s) {
+        info->sigma_increment[s] = pl.sig_inc[s];
+        info->radius_increment[s] = pl.r_inc[s];
+    }
+    info->radius_desc = pl.r_desc;
+    info->workspace_bytes = pl.bytes;
+    info->algorithmic_bytes = pl.algo_bytes;
+}
+
+// ---- point-pair pattern ------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): the state advances by the golden-ratio
+// increment and each output is the state passed through the two-multiply mixer.
+namespace {
+struct SplitMix64 {
+    uint64_t state;
+    uint64_t next() {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    // 53 random bits mapped to the open interval (0, 1)
+    double uniform() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    // Box-Muller, cosine branch only
+    double normal() {
+        const double u = uniform();
+        const double v = uniform();
+        return std::sqrt(-2.0 * std::log(u)) * std::cos(2.0 * 3.14159265358979323846 * v);
+    }
+};
+}  // namespace
+
+void make_pattern(const sift3d_params& p, float* out) {
+    SplitMix64 g{p.pattern_seed};
+    const double clip = 4.0;
+    for (int k = 0; k < SIFT3D_N_PAIRS; ++k) {
+        double p1[3], p2[3];
+        for (;;) {
+            for (int c = 0; c < 3; ++c) p1[c] = g.normal();
+            if (std::fabs(p1[0]) <= clip && std::fabs(p1[1]) <= clip && std::fabs(p1[2]) <= clip) break;
+        }
+        for (;;) {
+            for (int c = 0; c < 3; ++c) p2[c] = p1[c] + g.normal();
+            if (std::fabs(p2[0]) <= clip && std::fabs(p2[1]) <= clip && std::fabs(p2[2]) <= clip) break;
+        }
+        for (int c = 0; c < 3; ++c) {
+            out[k * 6 + c] = (float)p1[c];
+            out[k * 6 + 3 + c] = (float)p2[c];
+        }
+    }
+}
+
+// ---- workspaces -------------------------------------------------------------
+int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err) {
+    ws->plan = plan;
+    ws->capacity = capacity;
+    int n2 = 1;
+    while (n2 < capacity) n2 <<= 1;
+    ws->sort_len = capacity > 16384 ? n2 : 0;
+    const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
+    const size_t keys = round_up((size_t)ws->sort_len * 8, 256);
+    ws->bytes = plan.bytes + rec + keys + 256;
+    cudaError_t e = cudaMalloc(&ws->base, ws->bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        ws->base = nullptr;
+        if (err) *err = std::string("cudaMalloc of the workspace failed: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
+    }
+    // Padding columns are read (never used) by the column-linear z pass.
+    e = cudaMemset(ws->base, 0, ws->bytes);
+    if (e != cudaSuccess) {
+        if (err) *err = std::string("cudaMemset failed: ") + cudaGetErrorString(e);
+        return SIFT3D_ECUDA;
+    }
+    ws->staging = reinterpret_cast<sift3d_keypoint*>(ws->base + plan.bytes);
+    ws->sort_keys = ws->sort_len ? reinterpret_cast<unsigned long long*>(ws->base + plan.bytes + rec) : nullptr;
+    ws->count = reinterpret_cast<int*>(ws->base + plan.bytes + rec + keys);
+    ws->count_out = ws->count + 1;
+    return SIFT3D_OK;
+}
+
+void free_workspace(Workspace* ws) {
+    if (ws->base) cudaFree(ws->base);
+    ws->base = nullptr;
+}
+
+// ---- detect DAG ---------------------------------------------------------------
+std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* first_node, int* sort_node) {
+    const Plan& pl = ws.plan;
+    const int st = pl.p.storage;
+    std::vector<Node> nodes;
+    auto add = [&](const LaunchSpec& s, auto args, std::vector<int> deps) {
+        Node n;
+        n.spec = s;
+        n.set_args(args);
+        n.deps = std::move(deps);
+        nodes.push_back(std::move(n));
+        return (int)nodes.size() - 1;
+    };
+    std::vector<int> peak_nodes;
+    int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
+    *first_node = -1;
+    for (int o = 0; o < pl.nO; ++o) {
+        const OctaveGeom& g = pl.oct[o];
+        int prev = -1;  // node that produced G_{s-1}
+        for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
+            ConvXYArgs xa{};
+            xa.dst = ws.T(o);
+            xa.py = g.py;
+            xa.pz = g.pz;
+            xa.nx = g.nx;
+            xa.ny = g.ny;
+            xa.nz = g.nz;
+            xa.src_scale = 1.0f;
+            int src_kind = 2;
+            bool sub = false;
+            int radius;
+            std::vector<int> deps;
+            if (o == 0 && s == 0) {
+                xa.src = c.input;
+                xa.src_py = pl.nx;
+                xa.src_pz = (int64_t)pl.nx * pl.ny;
+                src_kind = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 0;
+                xa.src_scale = c.dtype == SIFT3D_DTYPE_U8 ? 1.0f / 255.0f : 1.0f;
+                xa.zero_count = ws.count;
+                xa.taps = pl.t_init;
+                radius = pl.r_init;
+            } else if (s == 1 && o > 0) {
+                sub = true;
+                xa.src = ws.G(o - 1, pl.S);
+                xa.src_py = pl.oct[o - 1].py;
+                xa.src_pz = pl.oct[o - 1].pz;
+                xa.base_out = ws.G(o, 0);
+                xa.taps = pl.t_inc[0];
+                radius = pl.r_inc[0];
+                deps.push_back(g_node[o - 1][pl.S]);
+            } else {
+                xa.src = ws.G(o, s - 1);
+                xa.src_py = g.py;
+                xa.src_pz = g.pz;
+                xa.taps = pl.t_inc[s - 1];
+                radius = pl.r_inc[s - 1];
+                deps.push_back(prev);
+            }
+            const int nxy = add(conv_xy_spec(radius, src_kind, st, sub, xa), xa, deps);
+            if (*first_node < 0) *first_node = nxy;
+            ConvZArgs za{};
+            za.src = ws.T(o);
+            za.dst = ws.G(o, s);
+            za.py = g.py;
+            za.pz = g.pz;
+            za.nx = g.nx;
+            za.ny = g.ny;
+            za.nz = g.nz;
+            za.taps = xa.taps;
+            if (s > 0) {
+                za.prev = ws.G(o, s - 1);
+                za.dog = ws.D(o, s - 1);
+            }
+            prev = add(conv_z_spec(radius, st, za), za, {nxy});
+            g_node[o][s] = prev;
+        }
+        if (o > 0) g_node[o][0] = g_node[o][1];
+        // peak detection on D_1..D_S
+        if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
+            PeakArgs pa{};
+            for (int s = 0; s < pl.nD; ++s) pa.dog[s] = ws.D(o, s);
+            pa.py = g.py;
+            pa.pz = g.pz;
+            pa.nx = g.nx;
+            pa.ny = g.ny;
+            pa.nz = g.nz;
+            pa.octave = o;
+            pa.n_scales = pl.S;
+            pa.border = pl.p.border;
+            pa.sign_sum_min = pl.p.sign_sum_min;
+            pa.contrast = (float)pl.p.contrast_thresh;
+            const double r = pl.p.curvature_r;
+            pa.curv_k1 = (float)((2.0 * r + 1.0) * (2.0 * r + 1.0) * (2.0 * r + 1.0));
+            pa.curv_k2 = (float)(r * r);
+            for (int s = 0; s < pl.L; ++s) pa.sigma_level[s] = (float)pl.sig_level[s];
+            pa.out = ws.staging;
+            pa.count = ws.count;
+            pa.capacity = ws.capacity;
+            peak_nodes.push_back(add(peak_spec(st, pa), pa, {g_node[o][pl.L - 1]}));
+        }
+        // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3)
+        if (pl.r_desc > 0) {
+            for (int s = 1; s <= pl.S; ++s) {
+                ConvXYArgs xa{};
+                xa.src = ws.G(o, s);
+                xa.src_py = g.py;
+                xa.src_pz = g.pz;
+                xa.src_scale = 1.0f;
+                xa.dst = ws.TB(o, s);
+                xa.py = g.py;
+                xa.pz = g.pz;
+                xa.nx = g.nx;
+                xa.ny = g.ny;
+                xa.nz = g.nz;
+                xa.taps = pl.t_desc;
+                const int nxy = add(conv_xy_spec(pl.r_desc, 2, st, false, xa), xa, {g_node[o][s]});
+                ConvZArgs za{};
+                za.src = ws.TB(o, s);
+                za.dst = ws.B(o, s);
+                za.py = g.py;
+                za.pz = g.pz;
+                za.nx = g.nx;
+                za.ny = g.ny;
+                za.nz = g.nz;
+                za.taps = pl.t_desc;
+                add(conv_z_spec(pl.r_desc, st, za), za, {nxy});
+            }
+        }
+    }
+    SortArgs sa{};
+    sa.staging = ws.staging;
+    sa.out = c.out;
+    sa.count = ws.count;
+    sa.count_out = ws.count_out;
+    sa.capacity = ws.capacity;
+    sa.scratch_keys = ws.sort_keys;
+    sa.scratch_len = ws.sort_len;
+    std::vector<int> deps = peak_nodes;
+    if (deps.empty() && *first_node >= 0) deps.push_back((int)nodes.size() - 1);
+    *sort_node = add(sort_spec(sa), sa, deps);
+    return nodes;
+}
+
+DescribeArgs make_describe_args(const Workspace& ws, const float* pattern) {
+    DescribeArgs a{};
+    const Plan& pl = ws.plan;
+    a.n_scales = pl.S;
+    a.n_octaves = pl.nO;
+    for (int o = 0; o < pl.nO; ++o)
+        for (int s = 1; s <= pl.S; ++s) {
+            DescLevel& L = a.lv[o][s - 1];
+            L.ptr = ws.B(o, s);
+            L.py = pl.oct[o].py;
+            L.pz = pl.oct[o].pz;
+            L.nx = pl.oct[o].nx;
+            L.ny = pl.oct[o].ny;
+            L.nz = pl.oct[o].nz;
+            L.sigma = (float)pl.sig_level[s];
+        }
+    memcpy(a.pattern, pattern, sizeof(a.pattern));
+    return a;
+}
+
+DetectExec::~DetectExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+}
+
+namespace {
+int cuda_fail(std::string* err, const char* what, cudaError_t e) {
+    if (err) *err = std::string(what) + ": " + cudaGetErrorString(e);
+    return SIFT3D_ECUDA;
+}
+
+cudaKernelNodeParams node_params(Node& n) {
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(n.spec.func);
+    kp.gridDim = n.spec.grid;
+    kp.blockDim = n.spec.block;
+    kp.sharedMemBytes = (unsigned)n.spec.smem;
+    kp.kernelParams = &n.argp;
+    kp.extra = nullptr;
+    return kp;
+}
+}  // namespace
+
+int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, cudaStream_t st,
+               std::string* err) {
+    if (ex.nodes.empty()) {
+        ex.nodes = build_detect(ws, c, &ex.first, &ex.sort);
+        for (auto& n : ex.nodes)
+            if (n.spec.func == nullptr) {
+                if (err) *err = "no kernel instance for this configuration";
+                ex.nodes.clear();
+                return SIFT3D_EINVAL;
+            }
+        ex.cur_input = c.input;
+        ex.cur_out = c.out;
+    } else if (ex.cur_input != c.input || ex.cur_out != c.out) {
+        // only the first conv (input) and the sort (output) see caller pointers
+        ConvXYArgs xa;
+        memcpy(&xa, ex.nodes[ex.first].arg.data(), sizeof(xa));
+        xa.src = c.input;
+        ex.nodes[ex.first].set_args(xa);
+        SortArgs sa;
+        memcpy(&sa, ex.nodes[ex.sort].arg.data(), sizeof(sa));
+        sa.out = c.out;
+        ex.nodes[ex.sort].set_args(sa);
+        if (ex.exec) {
+            for (int idx : {ex.first, ex.sort}) {
+                cudaKernelNodeParams kp = node_params(ex.nodes[idx]);
+                cudaError_t e = cudaGraphExecKernelNodeSetParams(ex.exec, ex.gnodes[idx], &kp);
+                if (e != cudaSuccess) return cuda_fail(err, "cudaGraphExecKernelNodeSetParams", e);
+            }
+        }
+        ex.cur_input = c.input;
+        ex.cur_out = c.out;
+    }
+    if (!use_graph) {
+        for (auto& n : ex.nodes) {
+            cudaError_t e = cudaLaunchKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st);
+            if (e != cudaSuccess) return cuda_fail(err, n.spec.name, e);
+        }
+        return SIFT3D_OK;
+    }
+    if (!ex.exec) {
+        cudaError_t e = cudaGraphCreate(&ex.graph, 0);
+        if (e != cudaSuccess) return cuda_fail(err, "cudaGraphCreate", e);
+        ex.gnodes.resize(ex.nodes.size());
+        for (size_t i = 0; i < ex.nodes.size(); ++i) {
+            std::vector<cudaGraphNode_t> deps;
+            for (int d : ex.nodes[i].deps) deps.push_back(ex.gnodes[d]);
+            cudaKernelNodeParams kp = node_params(ex.nodes[i]);
+            e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, deps.data(), deps.size(), &kp);
+            if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddKernelNode", e);
+        }
+        e = cudaGraphInstantiate(&ex.exec, ex.graph, 0);
+        if (e != cudaSuccess) return cuda_fail(err, "cudaGraphInstantiate", e);
+    }
+    cudaError_t e = cudaGraphLaunch(ex.exec, st);
+    if (e != cudaSuccess) return cuda_fail(err, "cudaGraphLaunch", e);
+    return SIFT3D_OK;
+}
+
+}  // namespace sift3d

@@ -1,0 +1,113 @@
+// Host runtime of the sift3d library: plans, device workspaces, the launch DAG
+// of one detect, and its execution as direct launches or as a CUDA graph.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sift3d {
+
+struct OctaveGeom {
+    int nx = 0, ny = 0, nz = 0;
+    int64_t py = 0, pz = 0;          // pitches in elements (py multiple of 8)
+    int64_t voxels() const { return (int64_t)nx * ny * nz; }
+};
+
+struct Plan {
+    sift3d_params p{};
+    int nx = 0, ny = 0, nz = 0;
+    int S = 0, L = 0, nD = 0;        // scales, Gaussian levels (S+3), DoGs (S+2)
+    int nO = 0;
+    OctaveGeom oct[SIFT3D_MAX_OCTAVES];
+    double sig_level[kMaxLevels] = {};
+    double sig_init = 0, sig_inc[kMaxLevels] = {}, sig_desc = 0;
+    int r_init = 0, r_inc[kMaxLevels] = {}, r_desc = 0;
+    Taps t_init{}, t_inc[kMaxLevels]{}, t_desc{};
+    size_t elem = 4;                 // bytes per stored pyramid value
+    // byte offsets into one workspace allocation
+    size_t off_G[SIFT3D_MAX_OCTAVES][kMaxLevels] = {};
+    size_t off_D[SIFT3D_MAX_OCTAVES][kMaxDogs] = {};
+    size_t off_B[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
+    size_t off_T[SIFT3D_MAX_OCTAVES] = {};
+    size_t off_TB[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
+    size_t bytes = 0;
+    uint64_t algo_bytes = 0;
+};
+
+// Validate params (without dims when nx <= 0) and build the plan.
+int validate_params(const sift3d_params& p, std::string* err);
+int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan* out, std::string* err);
+void fill_plan_info(const Plan& pl, sift3d_plan_info* info);
+void make_pattern(const sift3d_params& p, float* out);   // 64*6 floats
+
+// Device memory for one volume size: the whole pyramid plus detect scratch.
+struct Workspace {
+    Plan plan;
+    char* base = nullptr;
+    size_t bytes = 0;
+    sift3d_keypoint* staging = nullptr;   // unsorted records
+    int* count = nullptr;                 // running keypoint count
+    int* count_out = nullptr;             // total written by the sort
+    unsigned long long* sort_keys = nullptr;
+    int capacity = 0;
+    int sort_len = 0;
+    void* G(int o, int s) const { return base + plan.off_G[o][s]; }
+    void* D(int o, int s) const { return base + plan.off_D[o][s]; }
+    void* B(int o, int s) const {  // s = 1..S
+        return plan.r_desc > 0 ? (void*)(base + plan.off_B[o][s - 1]) : G(o, s);
+    }
+    float* T(int o) const { return reinterpret_cast<float*>(base + plan.off_T[o]); }
+    float* TB(int o, int s) const { return reinterpret_cast<float*>(base + plan.off_TB[o][s - 1]); }
+};
+
+int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
+void free_workspace(Workspace* ws);
+
+// One kernel launch of the detect DAG with its argument bytes and dependencies.
+struct Node {
+    LaunchSpec spec;
+    std::vector<unsigned long long> arg;   // 8-byte aligned copy of the arg struct
+    void* argp = nullptr;
+    std::vector<int> deps;
+    template <class A>
+    void set_args(const A& a) {
+        arg.assign((sizeof(A) + 7) / 8, 0ull);
+        memcpy(arg.data(), &a, sizeof(A));
+        argp = arg.data();
+    }
+};
+
+struct DetectCall {
+    const void* input;
+    int dtype;
+    sift3d_keypoint* out;
+    int capacity;
+};
+
+// Build the detect DAG (topologically ordered).  first_node / sort_node index
+// the two nodes that carry caller pointers.
+std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* first_node, int* sort_node);
+
+// A detect for one (shape, dtype, capacity), replayable as a CUDA graph.
+struct DetectExec {
+    std::vector<Node> nodes;
+    int first = -1, sort = -1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> gnodes;
+    const void* cur_input = nullptr;
+    sift3d_keypoint* cur_out = nullptr;
+    ~DetectExec();
+};
+
+int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, cudaStream_t st,
+               std::string* err);
+
+DescribeArgs make_describe_args(const Workspace& ws, const float* pattern);
+
+}  // namespace sift3d

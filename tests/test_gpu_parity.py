@@ -1,0 +1,206 @@
+"""CUDA path vs FP64 oracle, through the C ABI (needs a GPU).
+
+Sizes span several conv tiles (64x32 in xy, 16 in z) with ragged tails, the
+64^3 blob case, and the full 145x174x145 brain-like case in the same launch
+configuration bench.py times (CUDA graph, default parameters).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import sift3d_oracle as O  # noqa: E402
+from tests.parity import REL, compare_descriptors, compare_keypoints, level_error  # noqa: E402
+from workloads.volumes import blob_volume, brain_like_volume, to_uint8  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2112_10258_gb300 as S
+    return S
+
+
+def _oracle_params(**kw):
+    return O.Params(**kw)
+
+
+def _run(S, vol, capacity=16384, **params):
+    det = S.Sift3D(**params)
+    d = torch.from_numpy(vol).cuda()
+    buf, n = det.detect(d, capacity=capacity)
+    kps = S.keypoints_to_numpy(buf, min(n, capacity))
+    return det, buf, n, kps
+
+
+def _oracle_kps(kps):
+    out = np.zeros(kps.size, O.KEYPOINT_DTYPE)
+    for f in ("octave", "scale", "ix", "iy", "iz"):
+        out[f] = kps[f]
+    return out
+
+
+def _check_levels(S, det, ref, p):
+    worst = 0.0
+    for o, (Gs, Ds) in enumerate(zip(ref.pyramid.G, ref.pyramid.D)):
+        nz, ny, nx = Gs[0].shape
+        gmax = max(float(np.max(np.abs(g))) for g in Gs)
+        for s, g in enumerate(Gs):
+            e = level_error(det.read_level(o, S.LEVEL_GAUSS, s, (nx, ny, nz)).cpu().numpy(), g)
+            assert e <= REL, f"G[{o}][{s}] rel err {e}"
+            worst = max(worst, e)
+        for s, dv in enumerate(Ds):
+            e = level_error(det.read_level(o, S.LEVEL_DOG, s, (nx, ny, nz)).cpu().numpy(), dv, scale=gmax)
+            assert e <= REL, f"D[{o}][{s}] err {e} of max|G|"
+        if p.desc_blur_sigma > 0:
+            for s in range(1, p.scales_per_octave + 1):
+                b = O.blurred_level(ref.pyramid, o, s, p)
+                e = level_error(det.read_level(o, S.LEVEL_DESC, s, (nx, ny, nz)).cpu().numpy(), b)
+                assert e <= REL, f"B[{o}][{s}] rel err {e}"
+    return worst
+
+
+@pytest.mark.parametrize("shape,min_dim,seed", [
+    ((64, 64, 64), 16, 0),      # 64^3 blob case: 3 octaves
+    ((33, 17, 40), 8, 1),       # ragged in every axis, 2 octaves
+    ((70, 45, 37), 16, 2),      # x spans two tiles + tail, z spans three
+    ((130, 66, 20), 16, 3),     # x spans three tiles, single octave
+])
+def test_pyramid_levels_match_oracle(S, shape, min_dim, seed):
+    vol = blob_volume(seed=seed, shape=shape, n_blobs=20, sigma_range=(1.5, 4.0))
+    det, buf, n, kps = _run(S, vol, min_octave_dim=min_dim)
+    p = _oracle_params(min_octave_dim=min_dim)
+    ref = O.detect(vol, p)
+    _check_levels(S, det, ref, p)
+    compare_keypoints(kps, ref)
+    det.close()
+
+
+def _check_descriptors(S, det, buf, n, kps, ref, p):
+    if n == 0:
+        return 0
+    brief, rrief = det.describe(buf, n)
+    b = brief[:n].cpu().numpy().view(np.uint64)
+    r = rrief[: n * 64].cpu().numpy().reshape(n, 64)
+    dref = O.describe(ref.pyramid, _oracle_kps(kps), p)
+    return compare_descriptors(b, r, dref)
+
+
+def test_blob_case_64cubed_keypoints_and_descriptors(S):
+    vol = blob_volume(seed=0)
+    det, buf, n, kps = _run(S, vol)
+    p = _oracle_params()
+    ref = O.detect(vol, p)
+    exc, rep = compare_keypoints(kps, ref)
+    assert rep["gpu"] >= 20
+    _check_descriptors(S, det, buf, n, kps, ref, p)
+    det.close()
+
+
+@pytest.fixture(scope="module")
+def brain():
+    vol = brain_like_volume(seed=0)
+    p = _oracle_params()
+    return vol, p, O.detect(vol, p)
+
+
+def test_brain_full_size_graph_path(S, brain):
+    """145x174x145, default parameters, CUDA-graph launch path (as bench.py)."""
+    vol, p, ref = brain
+    det, buf, n, kps = _run(S, vol, capacity=16384, use_graphs=1)
+    exc, rep = compare_keypoints(kps, ref)
+    print("brain keypoints", rep)
+    assert rep["gpu"] > 800
+    _check_levels(S, det, ref, p)
+    dexc = _check_descriptors(S, det, buf, n, kps, ref, p)
+    print("descriptor exceptions", dexc)
+    det.close()
+
+
+def test_eager_and_graph_paths_bitwise_equal(S):
+    vol = blob_volume(seed=5, shape=(80, 72, 66), n_blobs=30)
+    outs = []
+    for g in (0, 1):
+        det, buf, n, kps = _run(S, vol, use_graphs=g)
+        brief, rrief = det.describe(buf, n)
+        lvl = det.read_level(0, S.LEVEL_GAUSS, 3, (80, 72, 66)).cpu().numpy()
+        outs.append((kps.tobytes(), brief[:n].cpu().numpy().tobytes(), rrief[: n * 64].cpu().numpy().tobytes(),
+                     lvl.tobytes()))
+        det.close()
+    assert outs[0] == outs[1]
+
+
+def test_graph_replay_with_new_buffers(S):
+    det = S.Sift3D()
+    results = []
+    for seed in (0, 1, 2):
+        vol = blob_volume(seed=seed)
+        d = torch.from_numpy(vol).cuda()
+        buf, n = det.detect(d, capacity=4096)
+        got = S.keypoints_to_numpy(buf, n)
+        ref = O.detect(vol, _oracle_params())
+        compare_keypoints(got, ref)
+        results.append(n)
+    assert len(set(results)) > 1
+    det.close()
+
+
+def test_uint8_input_converted_on_device(S):
+    vol = to_uint8(brain_like_volume(seed=3, shape=(64, 72, 60)))
+    det, buf, n, kps = _run(S, vol)
+    p = _oracle_params()
+    ref = O.detect(vol, p)
+    compare_keypoints(kps, ref)
+    _check_levels(S, det, ref, p)
+    det.close()
+
+
+def test_describe_with_device_count_matches_explicit_n(S):
+    vol = blob_volume(seed=2)
+    det, buf, n, kps = _run(S, vol, capacity=2048)
+    b1, r1 = det.describe(buf, n)
+    b2, r2 = det.describe(buf, -1, n_alloc=2048)
+    torch.cuda.synchronize()
+    assert torch.equal(b1[:n], b2[:n]) and torch.equal(r1[: n * 64], r2[: n * 64])
+    det.close()
+
+
+def test_capacity_overflow_reports_needed_count(S):
+    vol = blob_volume(seed=0)
+    det, buf, n_full, _ = _run(S, vol, capacity=4096)
+    assert n_full > 4
+    d = torch.from_numpy(vol).cuda()
+    out = torch.empty(4 * 48, dtype=torch.uint8, device="cuda")
+    from paper_2112_10258_gb300 import capi
+    rc, n = capi.sift3d_detect(det.ctx, d.data_ptr(), 0, 64, 64, 64, torch.cuda.current_stream().cuda_stream,
+                               out.data_ptr(), 4)
+    assert rc == capi.ECAPACITY and n == n_full
+    kept = S.keypoints_to_numpy(out, 4)
+    full = S.keypoints_to_numpy(buf, n_full)
+    assert set(map(tuple, np.stack([kept["octave"], kept["scale"], kept["iz"], kept["iy"], kept["ix"]], 1).tolist())) <= \
+        set(map(tuple, np.stack([full["octave"], full["scale"], full["iz"], full["iy"], full["ix"]], 1).tolist()))
+    det.close()
+
+
+@pytest.mark.parametrize("shape", [(8, 40, 40), (16, 16, 16), (1, 1, 1)])
+def test_degenerate_volumes(S, shape):
+    vol = blob_volume(seed=1, shape=shape, n_blobs=3)
+    det, buf, n, kps = _run(S, vol)
+    ref = O.detect(vol, _oracle_params())
+    compare_keypoints(kps, ref)
+    assert n == ref.keypoints.size
+    det.close()
+
+
+def test_constant_volume_has_no_keypoints(S):
+    vol = np.full((30, 40, 50), 0.25, np.float32)
+    det, buf, n, kps = _run(S, vol)
+    assert n == 0
+    g = det.read_level(0, S.LEVEL_DOG, 2, (50, 40, 30)).cpu().numpy()
+    assert np.max(np.abs(g)) < 1e-6
+    det.close()
