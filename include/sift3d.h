@@ -103,7 +103,8 @@ typedef struct sift3d_params {
     int32_t  max_octaves;        /* 0 = no limit                               */
     int32_t  sign_sum_min;       /* 80 = strict extremum; 1..80                */
     int32_t  border;             /* 1, >= 1                                    */
-    int32_t  reserved;           /* 0                                          */
+    int32_t  profile;            /* 0; 1 = time every detect kernel with CUDA
+                                    events (sift3d_stage_times)                */
     double   contrast_thresh;    /* 0.005 (compared in float32 on the device)  */
     double   curvature_r;        /* 10, > 1                                    */
     double   trunc;              /* 4.0  filter radius = ceil(trunc * sigma)   */
@@ -236,6 +237,20 @@ int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int 
  * Errors: SIFT3D_EINVAL (no prior detect, index out of range), SIFT3D_ECUDA. */
 int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index,
                       float* dev_dst, void* stream);
+
+/* Per-kernel device times of the last detect on ctx, when the context was
+ * created with params.profile = 1 (CUDA events recorded around every kernel of
+ * the detect, inside the graph when graphs are used).  Waits for that detect.
+ *   max      capacity of ms_out / names_out.
+ *   ms_out   host array, kernel i's elapsed milliseconds.
+ *   names_out host array of pointers to library-owned labels such as
+ *            "o0.s5.conv_z_dog" (octave 0, level 5); may be NULL.
+ *   algo_bytes_out host array, each kernel's algorithmic bytes (minimum reads
+ *            and writes of its inputs and outputs); may be NULL.
+ *   n_out    receives the number of kernels (may exceed max).
+ * Errors: SIFT3D_EINVAL (no prior detect or profiling off), SIFT3D_ECUDA. */
+int sift3d_stage_times(sift3d_ctx* ctx, int max, float* ms_out, const char** names_out,
+                       uint64_t* algo_bytes_out, int* n_out);
 
 /* Serving (no counterpart in the paper).  sift3d_submit copies a HOST volume
  * (the library reads it before returning, unless flags has

@@ -32,7 +32,7 @@ class Params(C.Structure):
     _fields_ = [
         ("sigma0", C.c_double), ("sigma_in", C.c_double), ("scales_per_octave", C.c_int32),
         ("min_octave_dim", C.c_int32), ("max_octaves", C.c_int32), ("sign_sum_min", C.c_int32),
-        ("border", C.c_int32), ("reserved", C.c_int32), ("contrast_thresh", C.c_double),
+        ("border", C.c_int32), ("profile", C.c_int32), ("contrast_thresh", C.c_double),
         ("curvature_r", C.c_double), ("trunc", C.c_double), ("desc_blur_sigma", C.c_double),
         ("desc_method", C.c_int32),
         ("pattern_seed", C.c_uint64), ("storage", C.c_int32), ("use_graphs", C.c_int32),
@@ -94,6 +94,8 @@ SIGNATURES = {
                                 C.POINTER(C.c_uint64)]),
     "sift3d_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(Result)]),
     "sift3d_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sift3d_stage_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_char_p),
+                                     C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
 }
 
 
@@ -188,3 +190,16 @@ def sift3d_poll(ctx, ticket, timeout_us) -> tuple[int, Result]:
 
 def sift3d_release(ctx, ticket) -> int:
     return _lib.sift3d_release(C.c_void_p(ctx), ticket)
+
+
+def sift3d_stage_times(ctx, max_n: int = 512):
+    """Returns (rc, [(label, ms, algorithmic_bytes), ...]) for the last detect."""
+    ms = (C.c_float * max_n)()
+    names = (C.c_char_p * max_n)()
+    ab = (C.c_uint64 * max_n)()
+    n = C.c_int(0)
+    rc = _lib.sift3d_stage_times(C.c_void_p(ctx), max_n, ms, names, ab, C.byref(n))
+    if rc != OK:
+        return rc, []
+    k = min(n.value, max_n)
+    return rc, [(names[i].decode(), float(ms[i]), int(ab[i])) for i in range(k)]

@@ -47,6 +47,7 @@ struct sift3d_ctx {
     int device = -1;
     std::map<ShapeKey, std::unique_ptr<DetectEntry>> cache;
     DetectEntry* last = nullptr;
+    int last_dtype = 0;
     std::unique_ptr<Server> server;
     std::mutex err_mu;
 };
@@ -112,7 +113,7 @@ int enqueue_detect(DetectEntry* ent, const void* vol, int dtype, sift3d_keypoint
         return SIFT3D_OK;
     }
     DetectCall call{vol, dtype, out, ent->ws.capacity};
-    return run_detect(ent->ws, *ent->ex[dtype], call, graphs, st, err);
+    return run_detect(ent->ws, *ent->ex[dtype], call, graphs, ent->ws.plan.p.profile != 0, st, err);
 }
 
 int enqueue_describe(const DetectEntry* ent, const float* pattern, const sift3d_keypoint* kps, int n, int kind,
@@ -483,6 +484,7 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
     rc = enqueue_detect(ent, dev_vol, dtype, dev_out, ctx->p.use_graphs != 0, st, &err);
     if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
     ctx->last = ent;
+    ctx->last_dtype = dtype;
     if (n_out) {
         int h = 0;
         cudaError_t e = cudaMemcpyAsync(&h, ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -541,6 +543,27 @@ int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index, float* d
     std::string err;
     rc = launch(read_level_spec(pl.p.storage, a), &a, static_cast<cudaStream_t>(stream), &err);
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
+}
+
+int sift3d_stage_times(sift3d_ctx* ctx, int max, float* ms_out, const char** names_out, uint64_t* algo_bytes_out,
+                       int* n_out) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->last || !ctx->last->ex[ctx->last_dtype]) return set_err(ctx, SIFT3D_EINVAL, "no prior detect");
+    const DetectExec& ex = *ctx->last->ex[ctx->last_dtype];
+    if (!ex.profile || ex.ev_end.empty()) return set_err(ctx, SIFT3D_EINVAL, "context created with profile = 0");
+    if (max < 0 || (max > 0 && !ms_out)) return set_err(ctx, SIFT3D_EINVAL, "bad output array");
+    const int n = (int)ex.nodes.size();
+    if (n_out) *n_out = n;
+    for (int i = 0; i < n && i < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(ex.ev_end[i]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ex.ev_begin[i], ex.ev_end[i]);
+        if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("stage_times: ") + cudaGetErrorString(e));
+        ms_out[i] = ms;
+        if (names_out) names_out[i] = ex.nodes[i].label.c_str();
+        if (algo_bytes_out) algo_bytes_out[i] = ex.nodes[i].algo_bytes;
+    }
+    return SIFT3D_OK;
 }
 
 int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype, int nx, int ny, int nz, int flags,

@@ -260,6 +260,14 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         nodes.push_back(std::move(n));
         return (int)nodes.size() - 1;
     };
+    auto tag = [&](int idx, const char* fmt, int a, int b, uint64_t bytes) {
+        char buf[64];
+        snprintf(buf, sizeof(buf), fmt, a, b, nodes[idx].spec.name);
+        nodes[idx].label = buf;
+        nodes[idx].algo_bytes = bytes;
+    };
+    const uint64_t e = pl.elem;
+    const uint64_t in_e = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 4;
     std::vector<int> peak_nodes;
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
     *first_node = -1;
@@ -307,6 +315,13 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             }
             const int nxy = add(conv_xy_spec(radius, src_kind, st, sub, xa), xa, deps);
             if (*first_node < 0) *first_node = nxy;
+            {
+                const uint64_t N = (uint64_t)g.voxels();
+                // reads its source once, writes the float32 intermediate
+                // (sub-sample mode: reads 8 source voxels per voxel, also writes G_0)
+                const uint64_t rd = (o == 0 && s == 0) ? in_e * N : (sub ? 8 * e * N : e * N);
+                tag(nxy, "o%d.s%d.%s", o, s, rd + 4 * N + (sub ? e * N : 0));
+            }
             ConvZArgs za{};
             za.src = ws.T(o);
             za.dst = ws.G(o, s);
@@ -321,6 +336,12 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 za.dog = ws.D(o, s - 1);
             }
             prev = add(conv_z_spec(radius, st, za), za, {nxy});
+            {
+                const uint64_t N = (uint64_t)g.voxels();
+                // reads the intermediate, writes G_s; with the DoG also reads
+                // G_{s-1} and writes D_{s-1}
+                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? 2 * e * N : 0));
+            }
             g_node[o][s] = prev;
         }
         if (o > 0) g_node[o][0] = g_node[o][1];
@@ -346,6 +367,8 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             pa.count = ws.count;
             pa.capacity = ws.capacity;
             peak_nodes.push_back(add(peak_spec(st, pa), pa, {g_node[o][pl.L - 1]}));
+            // D_1..D_S must be read in full; D_0 and D_{S+1} only around candidates
+            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
         }
         // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3)
         if (pl.r_desc > 0) {
@@ -363,6 +386,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 xa.nz = g.nz;
                 xa.taps = pl.t_desc;
                 const int nxy = add(conv_xy_spec(pl.r_desc, 2, st, false, xa), xa, {g_node[o][s]});
+                tag(nxy, "o%d.b%d.%s", o, s, (e + 4) * (uint64_t)g.voxels());
                 ConvZArgs za{};
                 za.src = ws.TB(o, s);
                 za.dst = ws.B(o, s);
@@ -372,7 +396,8 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 za.ny = g.ny;
                 za.nz = g.nz;
                 za.taps = pl.t_desc;
-                add(conv_z_spec(pl.r_desc, st, za), za, {nxy});
+                const int nz_ = add(conv_z_spec(pl.r_desc, st, za), za, {nxy});
+                tag(nz_, "o%d.b%d.%s", o, s, (4 + e) * (uint64_t)g.voxels());
             }
         }
     }
@@ -387,6 +412,8 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     std::vector<int> deps = peak_nodes;
     if (deps.empty() && *first_node >= 0) deps.push_back((int)nodes.size() - 1);
     *sort_node = add(sort_spec(sa), sa, deps);
+    tag(*sort_node, "o%d.x%d.%s", 0, 0, 0);
+    nodes[*sort_node].label = "sort";
     return nodes;
 }
 
@@ -413,6 +440,8 @@ DescribeArgs make_describe_args(const Workspace& ws, const float* pattern) {
 DetectExec::~DetectExec() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev_begin) cudaEventDestroy(e);
+    for (cudaEvent_t e : ev_end) cudaEventDestroy(e);
 }
 
 namespace {
@@ -433,9 +462,10 @@ cudaKernelNodeParams node_params(Node& n) {
 }
 }  // namespace
 
-int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, cudaStream_t st,
-               std::string* err) {
+int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, bool profile,
+               cudaStream_t st, std::string* err) {
     if (ex.nodes.empty()) {
+        ex.profile = profile;
         ex.nodes = build_detect(ws, c, &ex.first, &ex.sort);
         for (auto& n : ex.nodes)
             if (n.spec.func == nullptr) {
@@ -445,6 +475,15 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
             }
         ex.cur_input = c.input;
         ex.cur_out = c.out;
+        if (ex.profile) {
+            ex.ev_begin.resize(ex.nodes.size());
+            ex.ev_end.resize(ex.nodes.size());
+            for (size_t i = 0; i < ex.nodes.size(); ++i) {
+                cudaError_t e = cudaEventCreate(&ex.ev_begin[i]);
+                if (e == cudaSuccess) e = cudaEventCreate(&ex.ev_end[i]);
+                if (e != cudaSuccess) return cuda_fail(err, "cudaEventCreate", e);
+            }
+        }
     } else if (ex.cur_input != c.input || ex.cur_out != c.out) {
         // only the first conv (input) and the sort (output) see caller pointers
         ConvXYArgs xa;
@@ -466,9 +505,12 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         ex.cur_out = c.out;
     }
     if (!use_graph) {
-        for (auto& n : ex.nodes) {
+        for (size_t i = 0; i < ex.nodes.size(); ++i) {
+            Node& n = ex.nodes[i];
+            if (ex.profile) cudaEventRecord(ex.ev_begin[i], st);
             cudaError_t e = cudaLaunchKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st);
             if (e != cudaSuccess) return cuda_fail(err, n.spec.name, e);
+            if (ex.profile) cudaEventRecord(ex.ev_end[i], st);
         }
         return SIFT3D_OK;
     }
@@ -479,9 +521,20 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             std::vector<cudaGraphNode_t> deps;
             for (int d : ex.nodes[i].deps) deps.push_back(ex.gnodes[d]);
+            if (ex.profile) {   // begin event -> kernel -> end event
+                cudaGraphNode_t b;
+                e = cudaGraphAddEventRecordNode(&b, ex.graph, deps.data(), deps.size(), ex.ev_begin[i]);
+                if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddEventRecordNode", e);
+                deps.assign(1, b);
+            }
             cudaKernelNodeParams kp = node_params(ex.nodes[i]);
             e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, deps.data(), deps.size(), &kp);
             if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddKernelNode", e);
+            if (ex.profile) {
+                cudaGraphNode_t en;
+                e = cudaGraphAddEventRecordNode(&en, ex.graph, &ex.gnodes[i], 1, ex.ev_end[i]);
+                if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddEventRecordNode", e);
+            }
         }
         e = cudaGraphInstantiate(&ex.exec, ex.graph, 0);
         if (e != cudaSuccess) return cuda_fail(err, "cudaGraphInstantiate", e);

@@ -74,6 +74,8 @@ struct Node {
     std::vector<unsigned long long> arg;   // 8-byte aligned copy of the arg struct
     void* argp = nullptr;
     std::vector<int> deps;
+    std::string label;                     // e.g. "o0.s5.conv_z_dog"
+    uint64_t algo_bytes = 0;               // minimum bytes the kernel must move
     template <class A>
     void set_args(const A& a) {
         arg.assign((sizeof(A) + 7) / 8, 0ull);
@@ -102,11 +104,13 @@ struct DetectExec {
     std::vector<cudaGraphNode_t> gnodes;
     const void* cur_input = nullptr;
     sift3d_keypoint* cur_out = nullptr;
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_begin, ev_end;   // per node, when profiling
     ~DetectExec();
 };
 
-int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, cudaStream_t st,
-               std::string* err);
+int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, bool profile,
+               cudaStream_t st, std::string* err);
 
 DescribeArgs make_describe_args(const Workspace& ws, const float* pattern);
 

@@ -19,9 +19,8 @@ HEADER = os.path.join(ROOT, "include", "sift3d.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    import __graft_entry__  # noqa: F401  (builds on import of build())
-    from paper_2112_10258_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2112_10258_gb300 import capi
     return capi
 

@@ -65,7 +65,7 @@ def _smooth_noise_fft(rng, shape_zyx, sigma: float) -> np.ndarray:
     fy = np.fft.fftfreq(ny)[None, :, None]
     fx = np.fft.rfftfreq(nx)[None, None, :]
     f *= np.exp(-2.0 * np.pi ** 2 * sigma ** 2 * (fx ** 2 + fy ** 2 + fz ** 2))
-    return np.fft.irfftn(f, s=shape_zyx)
+    return np.fft.irfftn(f, s=shape_zyx, axes=(0, 1, 2))
 
 
 def brain_like_volume(seed: int = 0, shape=BRAIN_SHAPE, warp_sigma: float = 8.0,
