@@ -232,6 +232,19 @@ const int* sift3d_device_count(const sift3d_ctx* ctx);
 int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int kind,
                     uint64_t* dev_brief, uint8_t* dev_rrief, void* stream);
 
+/* Separable 3D Gaussian blur of a dense float32 volume (Sec. 2.2.2 "Gaussian
+ * Convolution": a y pass and an x pass per plane, then a z pass), with the
+ * library's discrete kernel w_k ~ exp(-k^2/2 sigma^2), |k| <= ceil(trunc*sigma)
+ * (trunc from the context's params), unit sum, clamp-to-edge borders.
+ *   dev_in, dev_out  dense nx*ny*nz float32 device arrays (x fastest); they
+ *                    must not overlap.
+ *   sigma            > 0, with ceil(trunc*sigma) <= 16.
+ * Scratch for the intermediate passes is device memory owned by ctx, allocated
+ * on first use and grown when a larger volume arrives.
+ * Errors: SIFT3D_EINVAL (arguments, sigma), SIFT3D_ENOMEM, SIFT3D_ECUDA. */
+int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, int nz,
+                         double sigma, float* dev_out, void* stream);
+
 /* Copy one pyramid level of the last detect into a dense float32 device array
  * dev_dst of dims[octave] voxels (x fastest).  kind = SIFT3D_LEVEL_*.
  * Errors: SIFT3D_EINVAL (no prior detect, index out of range), SIFT3D_ECUDA. */

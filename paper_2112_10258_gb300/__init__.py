@@ -109,6 +109,18 @@ class Sift3D:
         self._check(rc, "sift3d_describe")
         return brief, rrief
 
+    def gaussian_blur(self, vol, sigma: float, out=None, stream=None):
+        """Separable 3D Gaussian blur of a dense float32 CUDA tensor (nz, ny, nx)."""
+        import torch
+        assert vol.is_cuda and vol.dtype == torch.float32 and vol.is_contiguous() and vol.dim() == 3
+        nz, ny, nx = vol.shape
+        if out is None:
+            out = torch.empty_like(vol)
+        rc = capi.sift3d_gaussian_blur(self.ctx, vol.data_ptr(), nx, ny, nz, sigma, out.data_ptr(),
+                                       _stream_handle(stream))
+        self._check(rc, "sift3d_gaussian_blur")
+        return out
+
     def read_level(self, octave: int, kind: int, index: int, dims, stream=None):
         import torch
         nx, ny, nz = dims

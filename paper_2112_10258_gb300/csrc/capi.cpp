@@ -50,6 +50,8 @@ struct sift3d_ctx {
     int last_dtype = 0;
     std::unique_ptr<Server> server;
     std::mutex err_mu;
+    float* blur_scratch = nullptr;     // two pitched float32 volumes
+    int64_t blur_scratch_elems = 0;    // per volume
 };
 
 namespace {
@@ -460,6 +462,7 @@ void sift3d_destroy(sift3d_ctx* ctx) {
     ctx->server.reset();
     if (ctx->device >= 0) cudaDeviceSynchronize();
     ctx->cache.clear();
+    if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
     delete ctx;
 }
 
@@ -515,6 +518,36 @@ int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int 
     std::string err;
     rc = enqueue_describe(ctx->last, ctx->pattern, dev_kps, n, kind, dev_brief, dev_rrief,
                           static_cast<cudaStream_t>(stream), &err);
+    return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
+}
+
+int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, int nz, double sigma,
+                         float* dev_out, void* stream) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!dev_in || !dev_out) return set_err(ctx, SIFT3D_EINVAL, "dev_in / dev_out is NULL");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4095 || ny > 4095 || nz > 4095)
+        return set_err(ctx, SIFT3D_EINVAL, "each dimension must be in 1..4095");
+    const int R = gaussian_radius(sigma, ctx->p.trunc);
+    if (!(sigma > 0.0) || R < 1 || R > kMaxRadius)
+        return set_err(ctx, SIFT3D_EINVAL, "sigma must be > 0 with ceil(trunc*sigma) <= 16");
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    const int64_t need = blur_pitch_elems(nx, ny, nz);
+    if (need > ctx->blur_scratch_elems) {
+        if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
+        ctx->blur_scratch = nullptr;
+        ctx->blur_scratch_elems = 0;
+        cudaError_t e = cudaMalloc(&ctx->blur_scratch, (size_t)need * 2 * sizeof(float));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            ctx->blur_scratch = nullptr;
+            return set_err(ctx, SIFT3D_ENOMEM, std::string("blur scratch: ") + cudaGetErrorString(e));
+        }
+        ctx->blur_scratch_elems = need;
+    }
+    std::string err;
+    rc = enqueue_blur(dev_in, nx, ny, nz, sigma, ctx->p.trunc, ctx->blur_scratch,
+                      ctx->blur_scratch + ctx->blur_scratch_elems, dev_out, static_cast<cudaStream_t>(stream), &err);
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
 }
 

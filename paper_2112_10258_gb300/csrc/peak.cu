@@ -22,6 +22,32 @@ constexpr int PK_BX = 32;
 constexpr int PK_BY = 8;
 constexpr int PK_THREADS = PK_BX * PK_BY;
 
+// The 80 neighbours as (dx, dy, dz, level offset): the 26 of D_s first (faces,
+// then edges, then corners: the likeliest to break an extremum early), then the
+// 27 of D_{s-1} and the 27 of D_{s+1}.
+struct NbrTable {
+    int4 v[80];
+};
+
+constexpr NbrTable make_nbr_table() {
+    NbrTable t{};
+    int n = 0;
+    for (int order = 1; order <= 3; ++order)          // |dx|+|dy|+|dz|
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int m = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (m == order) t.v[n++] = int4{dx, dy, dz, 0};
+                }
+    for (int dl = -1; dl <= 1; dl += 2)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) t.v[n++] = int4{dx, dy, dz, dl};
+    return t;
+}
+
+__constant__ int4 c_nbr[80];
+
 template <typename S>
 __device__ __forceinline__ float ldv(const void* base, int64_t off) {
     return to_f32(static_cast<const S*>(base)[off]);
@@ -45,20 +71,18 @@ __global__ void __launch_bounds__(PK_THREADS) peak_kernel(const PeakArgs a) {
             const float c = ldv<S>(a.dog[s], off);
             cval[s] = c;
             if (!(fabsf(c) >= a.contrast)) continue;
+            // Sum of signs with early exit: after k of the 80 comparisons, |S| can
+            // change by at most 80 - k, so stop once the cut is out of reach.
             int sum = 0;
-            for (int l = s - 1; l <= s + 1; ++l) {
-                const void* D = a.dog[l];
-#pragma unroll
-                for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            if (l == s && dz == 0 && dy == 0 && dx == 0) continue;
-                            const float n = ldv<S>(D, off + dz * pz + dy * py + dx);
-                            sum += (c > n) - (c < n);
-                        }
+            int k = 0;
+            for (; k < 80; ++k) {
+                const int4 nb = c_nbr[k];
+                const float n = ldv<S>(a.dog[s + nb.w], off + nb.z * pz + nb.y * py + nb.x);
+                sum += (c > n) - (c < n);
+                const int reach = (sum < 0 ? -sum : sum) + (79 - k);
+                if (reach < a.sign_sum_min) break;
             }
+            if (k < 80) continue;
             ssum[s] = sum;
             if (sum < a.sign_sum_min && sum > -a.sign_sum_min) continue;
             const void* D = a.dog[s];
@@ -183,7 +207,13 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
 }  // namespace
 
 LaunchSpec peak_spec(int storage, const PeakArgs& a) {
+    static const bool table_ready = [] {
+        constexpr NbrTable t = make_nbr_table();
+        static_assert(t.v[25].w == 0 && t.v[26].w == -1 && t.v[79].w == 1, "neighbour table layout");
+        return cudaMemcpyToSymbol(c_nbr, t.v, sizeof(t.v)) == cudaSuccess;
+    }();
     LaunchSpec s;
+    if (!table_ready) return s;
     if (storage == SIFT3D_STORAGE_F32) s.func = reinterpret_cast<const void*>(&peak_kernel<float>);
     else if (storage == SIFT3D_STORAGE_F16) s.func = reinterpret_cast<const void*>(&peak_kernel<__half>);
     else s.func = reinterpret_cast<const void*>(&peak_kernel<__nv_bfloat16>);

@@ -15,8 +15,12 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int radius_of(double sigma, double trunc) { return (int)std::ceil(trunc * sigma); }
 
+}  // namespace
+
+int gaussian_radius(double sigma, double trunc) { return radius_of(sigma, trunc); }
+
 // Sampled Gaussian on |k| <= R, normalised to unit sum in double, then float.
-Taps make_taps(double sigma, int R) {
+Taps gaussian_taps(double sigma, int R) {
     Taps t{};
     double w[kMaxRadius + 1];
     double sum = 0.0;
@@ -27,6 +31,10 @@ Taps make_taps(double sigma, int R) {
     for (int k = 0; k <= R; ++k) t.w[k] = (float)(w[k] / sum);
     return t;
 }
+
+namespace {
+
+Taps make_taps(double sigma, int R) { return gaussian_taps(sigma, R); }
 
 int fail(std::string* err, const char* msg) {
     if (err) *err = msg;
@@ -415,6 +423,63 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     tag(*sort_node, "o%d.x%d.%s", 0, 0, 0);
     nodes[*sort_node].label = "sort";
     return nodes;
+}
+
+int64_t blur_pitch_elems(int nx, int ny, int nz) {
+    return (int64_t)round_up((size_t)nx, 8) * ny * nz;
+}
+
+int enqueue_blur(const float* in, int nx, int ny, int nz, double sigma, double trunc, float* t, float* u,
+                 float* out, cudaStream_t st, std::string* err) {
+    const int R = radius_of(sigma, trunc);
+    if (!(sigma > 0.0) || R < 1 || R > kMaxRadius) {
+        if (err) *err = "sigma must be > 0 with ceil(trunc*sigma) in 1..16";
+        return SIFT3D_EINVAL;
+    }
+    const int64_t py = (int64_t)round_up((size_t)nx, 8), pz = py * ny;
+    ConvXYArgs xa{};
+    xa.src = in;
+    xa.src_py = nx;
+    xa.src_pz = (int64_t)nx * ny;
+    xa.src_scale = 1.0f;
+    xa.dst = t;
+    xa.py = py;
+    xa.pz = pz;
+    xa.nx = nx;
+    xa.ny = ny;
+    xa.nz = nz;
+    xa.taps = gaussian_taps(sigma, R);
+    ConvZArgs za{};
+    za.src = t;
+    za.dst = u;
+    za.py = py;
+    za.pz = pz;
+    za.nx = nx;
+    za.ny = ny;
+    za.nz = nz;
+    za.taps = xa.taps;
+    ReadLevelArgs ra{};
+    ra.src = u;
+    ra.py = py;
+    ra.pz = pz;
+    ra.nx = nx;
+    ra.ny = ny;
+    ra.nz = nz;
+    ra.dst = out;
+    const LaunchSpec s1 = conv_xy_spec(R, 0, SIFT3D_STORAGE_F32, false, xa);
+    const LaunchSpec s2 = conv_z_spec(R, SIFT3D_STORAGE_F32, za);
+    const LaunchSpec s3 = read_level_spec(SIFT3D_STORAGE_F32, ra);
+    void* a1 = &xa;
+    void* a2 = &za;
+    void* a3 = &ra;
+    cudaError_t e = cudaLaunchKernel(s1.func, s1.grid, s1.block, &a1, s1.smem, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(s2.func, s2.grid, s2.block, &a2, s2.smem, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(s3.func, s3.grid, s3.block, &a3, s3.smem, st);
+    if (e != cudaSuccess) {
+        if (err) *err = std::string("blur launch: ") + cudaGetErrorString(e);
+        return SIFT3D_ECUDA;
+    }
+    return SIFT3D_OK;
 }
 
 DescribeArgs make_describe_args(const Workspace& ws, const float* pattern) {

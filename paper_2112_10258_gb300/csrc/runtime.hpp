@@ -114,4 +114,15 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
 
 DescribeArgs make_describe_args(const Workspace& ws, const float* pattern);
 
+// Sampled Gaussian taps (unit sum) and their radius ceil(trunc * sigma).
+int gaussian_radius(double sigma, double trunc);
+Taps gaussian_taps(double sigma, int radius);
+
+// Pitch of the intermediate volumes of a standalone blur of an nx*ny*nz volume.
+int64_t blur_pitch_elems(int nx, int ny, int nz);
+// Enqueue a standalone separable blur: dense float32 in -> dense float32 out,
+// through two pitched float32 scratch volumes t and u of blur_pitch_elems each.
+int enqueue_blur(const float* in, int nx, int ny, int nz, double sigma, double trunc, float* t, float* u,
+                 float* out, cudaStream_t st, std::string* err);
+
 }  // namespace sift3d

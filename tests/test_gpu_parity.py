@@ -204,3 +204,14 @@ def test_constant_volume_has_no_keypoints(S):
     g = det.read_level(0, S.LEVEL_DOG, 2, (50, 40, 30)).cpu().numpy()
     assert np.max(np.abs(g)) < 1e-6
     det.close()
+
+
+@pytest.mark.parametrize("shape,sigma", [((37, 29, 23), 1.2263), ((145, 174, 145), 3.09), ((70, 45, 37), 0.95),
+                                         ((130, 66, 20), 4.0)])
+def test_gaussian_blur_matches_oracle(S, shape, sigma):
+    vol = blob_volume(seed=11, shape=shape, n_blobs=15)
+    det = S.Sift3D()
+    got = det.gaussian_blur(torch.from_numpy(vol).cuda(), sigma).cpu().numpy()
+    ref = O.blur3d(vol, sigma)
+    assert level_error(got, ref) <= REL
+    det.close()
