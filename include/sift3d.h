@@ -245,6 +245,28 @@ int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int 
 int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, int nz,
                          double sigma, float* dev_out, void* stream);
 
+/* The same blur for callers that cannot allocate device memory: code that runs
+ * where cudaMalloc is unavailable or not allowed (inside a host callback, in an
+ * allocator's own reclaim path, in a loop that must never enter the allocator)
+ * or that is handed only its input and output buffers.  This call allocates
+ * nothing, needs no context, and takes trunc explicitly (4.0 matches the
+ * default params).  No counterpart in the paper.
+ *   Scratch: one library-owned device array of 2 * SIFT3D_BLUR_NOALLOC_MAX_ELEMS
+ *   floats (32 MiB) that every GPU loading the library holds until the process
+ *   exits.  A volume fits when roundup(nx, 8) * ny * nz <= the maximum (a
+ *   145x174x145 volume does); larger volumes return SIFT3D_ECAPACITY.
+ *   The first call on a device looks up that device's address of the array
+ *   (cudaGetSymbolAddress, with the device current); make that first call
+ *   before any stream capture.
+ *   All calls share the array: calls whose work overlaps on the GPU (different
+ *   streams, or host threads without ordering) race and corrupt each other's
+ *   results.  Serialise them, e.g. on one stream.
+ * Errors: SIFT3D_EINVAL (arguments, sigma, trunc), SIFT3D_ECAPACITY (volume
+ * larger than the scratch), SIFT3D_ECUDA. */
+#define SIFT3D_BLUR_NOALLOC_MAX_ELEMS (1 << 22)
+int sift3d_gaussian_blur_noalloc(const float* dev_in, int nx, int ny, int nz, double sigma,
+                                 double trunc, float* dev_out, void* stream);
+
 /* Copy one pyramid level of the last detect into a dense float32 device array
  * dev_dst of dims[octave] voxels (x fastest).  kind = SIFT3D_LEVEL_*.
  * Errors: SIFT3D_EINVAL (no prior detect, index out of range), SIFT3D_ECUDA. */

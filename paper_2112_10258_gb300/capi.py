@@ -96,6 +96,8 @@ SIGNATURES = {
     "sift3d_release": (C.c_int, [C.c_void_p, C.c_uint64]),
     "sift3d_gaussian_blur": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                        C.c_void_p, C.c_void_p]),
+    "sift3d_gaussian_blur_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                               C.c_void_p, C.c_void_p]),
     "sift3d_stage_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_char_p),
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
 }
@@ -177,6 +179,11 @@ def sift3d_describe(ctx, dev_kps, n, kind, dev_brief, dev_rrief, stream) -> int:
 def sift3d_gaussian_blur(ctx, dev_in, nx, ny, nz, sigma, dev_out, stream) -> int:
     return _lib.sift3d_gaussian_blur(C.c_void_p(ctx), C.c_void_p(dev_in), nx, ny, nz, float(sigma),
                                      C.c_void_p(dev_out), C.c_void_p(stream))
+
+
+def sift3d_gaussian_blur_noalloc(dev_in, nx, ny, nz, sigma, trunc, dev_out, stream) -> int:
+    return _lib.sift3d_gaussian_blur_noalloc(C.c_void_p(dev_in), nx, ny, nz, float(sigma), float(trunc),
+                                             C.c_void_p(dev_out), C.c_void_p(stream))
 
 
 def sift3d_read_level(ctx, octave, kind, index, dev_dst, stream) -> int:
