@@ -116,6 +116,11 @@ typedef struct sift3d_params {
     uint64_t hbm_budget_bytes;   /* serving admission budget (0 = 40 GiB)      */
     int32_t  max_keypoints;      /* serving: keypoints kept per request (8192) */
     int32_t  max_inflight;       /* serving: requests on the device at once (4) */
+    int32_t  fuse_small_octaves; /* 0 = one launch per pass (default); 1 =
+                                    octaves after the first (<= 4M voxels) run
+                                    in one cooperative launch                  */
+    int32_t  use_pdl;            /* 1 = chain the detect graph's kernels with
+                                    programmatic dependent launch              */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

@@ -423,6 +423,8 @@ int sift3d_default_params(sift3d_params* out) {
     out->hbm_budget_bytes = 40ull << 30;
     out->max_keypoints = 8192;
     out->max_inflight = 4;
+    out->fuse_small_octaves = 0;
+    out->use_pdl = 1;
     return SIFT3D_OK;
 }
 
@@ -493,7 +495,7 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
         cudaError_t e = cudaMemcpyAsync(&h, ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("detect: ") + cudaGetErrorString(e));
-        if (h < 0) return set_err(ctx, SIFT3D_ECUDA, "keypoint sort had no scratch space");
+        if (h == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "octave-tail barrier wait ran out");
         *n_out = h;
         if (h > capacity) return set_err(ctx, SIFT3D_ECAPACITY, "more keypoints than capacity");
     }

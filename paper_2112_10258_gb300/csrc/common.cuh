@@ -16,6 +16,7 @@ namespace sift3d {
 constexpr int kMaxRadius = 16;     // largest 1D filter radius with a kernel instance
 constexpr int kMaxLevels = SIFT3D_MAX_SCALES + 3;
 constexpr int kMaxDogs = SIFT3D_MAX_SCALES + 2;
+constexpr int kSortSmemKeys = 4096;  // sort keys staged in shared memory per tile
 
 // ---- storage types: levels may be stored narrower than the float32 arithmetic
 __device__ __forceinline__ float to_f32(float v) { return v; }
@@ -29,6 +30,14 @@ template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
+
+// Programmatic dependent launch: a kernel lets its dependents start launching
+// (they are scheduled once every CTA of this grid has started) and waits for
+// its own predecessors' completion and memory before touching their outputs.
+// Both are no-ops for a kernel that was not launched as a programmatic
+// dependent.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Taps of a symmetric 1D Gaussian: w[0] is the centre, w[k] the weight at +-k.
 struct Taps {
@@ -48,9 +57,13 @@ struct ConvXYArgs {
     int64_t py, pz;           // pitches of dst / base_out
     int nx, ny, nz;           // dims of this octave
     void* base_out;           // sub mode: G_0 of this octave (storage type), else null
-    int* zero_count;          // if set, block (0,0,0) zeroes this counter first
+    int* zero_count;          // if set, block (0,0,0) zeroes kDetectCounters ints first
     Taps taps;
 };
+
+// Per-detect device counters: [0] keypoints found, [1] total reported by the
+// sort (-2 = a tail-kernel barrier wait ran out), [2] tail barrier, [3] tail error.
+constexpr int kDetectCounters = 4;
 
 // ---- conv_z: z pass over columns, epilogue writes G_s and the DoG -------------
 struct ConvZArgs {
@@ -81,10 +94,9 @@ struct SortArgs {
     const sift3d_keypoint* staging;
     sift3d_keypoint* out;
     const int* count;
+    const int* tail_err;        // non-zero: the detect failed, report -2
     int* count_out;             // total detected (may exceed capacity)
     int capacity;
-    unsigned long long* scratch_keys;  // >= next_pow2(capacity) entries, for large n
-    int scratch_len;
 };
 
 // ---- descriptors --------------------------------------------------------------
@@ -115,6 +127,26 @@ struct ReadLevelArgs {
     float* dst;
 };
 
+// ---- octave-tail kernel: phases of tile tasks in one cooperative launch -------
+struct TailTask {
+    enum Type : int { XY = 0, XY_SUB = 1, Z = 2, PEAK = 3 };
+    int type;
+    int radius;
+    int n_tiles;
+    int reserved;
+    ConvXYArgs xy;
+    ConvZArgs z;
+    PeakArgs pk;
+};
+
+struct TailArgs {
+    const TailTask* tasks;
+    const int* phase_begin;     // n_phases + 1 entries into tasks
+    int n_phases;
+    int* bar;                   // monotone barrier counter (zeroed per detect)
+    int* err;                   // set when a barrier wait runs out
+};
+
 // A kernel launch with its single by-value argument struct, usable both for a
 // direct launch and as a CUDA graph kernel node.
 struct LaunchSpec {
@@ -132,5 +164,8 @@ LaunchSpec peak_spec(int storage, const PeakArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
+LaunchSpec tail_spec(int storage, int n_scales, int max_ctas);
+int tail_tiles(const TailTask& t);
+int tail_smem_bytes(int n_scales);
 
 }  // namespace sift3d

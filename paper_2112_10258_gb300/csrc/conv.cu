@@ -16,171 +16,93 @@
 //
 // Every 1D pass is out[i] = sum_{k=-R..R} w_|k| in[clamp(i+k)], summed in
 // ascending k, in float32.
-#include "common.cuh"
+#include "conv_tile.cuh"
 
 namespace sift3d {
 
 namespace {
 
-constexpr int XY_TX = 64;
-constexpr int XY_TY = 32;
-constexpr int XY_J = 8;          // outputs per thread in each pass
-constexpr int XY_THREADS = 256;
-constexpr int Z_TZ = 16;
-constexpr int Z_THREADS = 256;
-
-template <int R>
-struct XYGeom {
-    static constexpr int W = XY_TX + 2 * R;         // staged columns
-    static constexpr int H = XY_TY + 2 * R;         // staged rows
-    static constexpr int WP = W | 1;                // odd pitch: no bank conflicts
-    static constexpr int SMEM = (H + XY_TY) * WP * 4;
-};
-
-template <typename T>
-__device__ __forceinline__ float load_f(const T* p) { return to_f32(*p); }
+using namespace conv_detail;
 
 template <int R, typename Tin, bool SUB, typename Tbase>
 __global__ void __launch_bounds__(XY_THREADS) conv_xy_kernel(const ConvXYArgs a) {
-    using G = XYGeom<R>;
     extern __shared__ float sm[];
-    float* in = sm;                       // H x WP staged source
-    float* mid = sm + G::H * G::WP;       // TY x WP after the y pass
-    const int x0 = blockIdx.x * XY_TX;
-    const int y0 = blockIdx.y * XY_TY;
-    const int z = blockIdx.z;
+    pdl_launch_dependents();
+    pdl_wait();
+    conv_xy_tile<R, Tin, SUB, Tbase>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+}
+
+template <int R, int TY, typename Tin, bool SUB, typename Tbase>
+__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
+    extern __shared__ float sm[];
+    pdl_launch_dependents();
+    pdl_wait();
+    const int nx = a.nx;
+    const int WP = row_pitch(nx);
+    float* in = sm;                          // (TY + 2R) x WP
+    float* mid = sm + (TY + 2 * R) * WP;     // TY x WP
+    const int y0 = blockIdx.x * TY;
+    const int z = blockIdx.y;
+    const int c = threadIdx.x;
     const Tin* src = static_cast<const Tin*>(a.src);
-    if (a.zero_count != nullptr && x0 == 0 && y0 == 0 && z == 0 && threadIdx.x == 0) *a.zero_count = 0;
+    if (a.zero_count != nullptr && y0 == 0 && z == 0 && c < kDetectCounters) a.zero_count[c] = 0;
 
-    for (int i = threadIdx.x; i < G::H * G::W; i += XY_THREADS) {
-        const int r = i / G::W;
-        const int c = i - r * G::W;
-        const int gy = min(max(y0 - R + r, 0), a.ny - 1);
-        const int gx = min(max(x0 - R + c, 0), a.nx - 1);
-        float v;
-        if constexpr (!SUB) {
-            v = load_f(src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py + gx) * a.src_scale;
-        } else {
-            const Tin* p = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy) * a.src_py + 2 * gx;
-            float acc = 0.f;
-            acc += load_f(p);
-            acc += load_f(p + 1);
-            acc += load_f(p + a.src_py);
-            acc += load_f(p + a.src_py + 1);
-            acc += load_f(p + a.src_pz);
-            acc += load_f(p + a.src_pz + 1);
-            acc += load_f(p + a.src_pz + a.src_py);
-            acc += load_f(p + a.src_pz + a.src_py + 1);
-            v = acc * 0.125f;
-            const int ty = r - R, tx = c - R;
-            if (ty >= 0 && ty < XY_TY && tx >= 0 && tx < XY_TX && y0 + ty < a.ny && x0 + tx < a.nx) {
-                static_cast<Tbase*>(a.base_out)[(int64_t)z * a.pz + (int64_t)(y0 + ty) * a.py + x0 + tx] =
-                    from_f32<Tbase>(v);
-            }
+    if (c < nx) {
+        float v[TY + 2 * R];
+#pragma unroll
+        for (int r = 0; r < TY + 2 * R; ++r) {
+            const int gy = min(max(y0 - R + r, 0), a.ny - 1);
+            v[r] = stage_value<Tin, SUB>(a, src, z, gy, c);
         }
-        in[r * G::WP + c] = v;
-    }
-    __syncthreads();
-
-    // y pass: item = (column c, group of J rows)
-    for (int item = threadIdx.x; item < G::W * (XY_TY / XY_J); item += XY_THREADS) {
-        const int c = item % G::W;
-        const int r0 = (item / G::W) * XY_J;
-        float v[XY_J + 2 * R];
+        if constexpr (SUB) {   // this CTA's own rows of the sub-sampled level are G_0
 #pragma unroll
-        for (int t = 0; t < XY_J + 2 * R; ++t) v[t] = in[(r0 + t) * G::WP + c];
+            for (int r = 0; r < TY; ++r)
+                if (y0 + r < a.ny)
+                    static_cast<Tbase*>(a.base_out)[(int64_t)z * a.pz + (int64_t)(y0 + r) * a.py + c] =
+                        from_f32<Tbase>(v[R + r]);
+        }
+        // y pass straight from the register window
 #pragma unroll
-        for (int j = 0; j < XY_J; ++j) {
+        for (int j = 0; j < TY; ++j) {
             float acc = 0.f;
 #pragma unroll
             for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
-            mid[(r0 + j) * G::WP + c] = acc;
+            mid[j * WP + c] = acc;
         }
     }
     __syncthreads();
 
-    // x pass: item = (row r, group of J columns); J contiguous outputs per thread
-    for (int item = threadIdx.x; item < XY_TY * (XY_TX / XY_J); item += XY_THREADS) {
-        const int r = item % XY_TY;
-        const int c0 = (item / XY_TY) * XY_J;
+    // x pass: item = (row r, group g of 8 columns), r fastest so a warp's lanes
+    // read different rows (odd pitch: no bank conflicts)
+    const int groups = (nx + ROW_J - 1) / ROW_J;
+    for (int item = threadIdx.x; item < TY * groups; item += blockDim.x) {
+        const int r = item % TY;
+        const int g = item / TY;
         const int y = y0 + r;
         if (y >= a.ny) continue;
-        float v[XY_J + 2 * R];
+        const int x0 = g * ROW_J;
+        float v[ROW_J + 2 * R];
 #pragma unroll
-        for (int t = 0; t < XY_J + 2 * R; ++t) v[t] = mid[r * G::WP + c0 + t];
-        float o[XY_J];
+        for (int t = 0; t < ROW_J + 2 * R; ++t) v[t] = mid[r * WP + min(max(x0 - R + t, 0), nx - 1)];
+        float o[ROW_J];
 #pragma unroll
-        for (int j = 0; j < XY_J; ++j) {
+        for (int j = 0; j < ROW_J; ++j) {
             float acc = 0.f;
 #pragma unroll
             for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
             o[j] = acc;
         }
-        float* dst = a.dst + (int64_t)z * a.pz + (int64_t)y * a.py + x0 + c0;
-        // The row pitch is a multiple of 8 elements, so writing the padding
-        // columns beyond nx stays inside the row; rows are 32-byte aligned.
-        if (x0 + c0 < a.nx) {
-            reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
-            reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
-        }
+        float* dst = a.dst + (int64_t)z * a.pz + (int64_t)y * a.py + x0;
+        reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
     }
 }
 
-template <typename S> struct Pair;
-template <> struct Pair<float> {
-    static __device__ __forceinline__ float2 load(const void* p) { return *static_cast<const float2*>(p); }
-    static __device__ __forceinline__ void store(void* p, float a, float b) {
-        *static_cast<float2*>(p) = make_float2(a, b);
-    }
-};
-template <> struct Pair<__half> {
-    static __device__ __forceinline__ float2 load(const void* p) {
-        return __half22float2(*static_cast<const __half2*>(p));
-    }
-    static __device__ __forceinline__ void store(void* p, float a, float b) {
-        *static_cast<__half2*>(p) = __floats2half2_rn(a, b);
-    }
-};
-template <> struct Pair<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 load(const void* p) {
-        return __bfloat1622float2(*static_cast<const __nv_bfloat162*>(p));
-    }
-    static __device__ __forceinline__ void store(void* p, float a, float b) {
-        *static_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-    }
-};
-
 template <int R, typename S>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
-    // Columns are addressed linearly inside a plane (pitch layout, padding
-    // columns included): the z pass does not care about x/y structure.
-    const int64_t col = ((int64_t)blockIdx.x * Z_THREADS + threadIdx.x) * 2;
-    if (col >= a.pz) return;
-    const int z0 = blockIdx.y * Z_TZ;
-    float2 v[Z_TZ + 2 * R];
-#pragma unroll
-    for (int t = 0; t < Z_TZ + 2 * R; ++t) {
-        const int zz = min(max(z0 - R + t, 0), a.nz - 1);
-        v[t] = *reinterpret_cast<const float2*>(a.src + (int64_t)zz * a.pz + col);
-    }
-#pragma unroll
-    for (int j = 0; j < Z_TZ; ++j) {
-        const int z = z0 + j;
-        if (z >= a.nz) break;
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int k = -R; k <= R; ++k) {
-            const float w = a.taps.w[k < 0 ? -k : k];
-            ax = fmaf(w, v[j + R + k].x, ax);
-            ay = fmaf(w, v[j + R + k].y, ay);
-        }
-        const int64_t off = (int64_t)z * a.pz + col;
-        Pair<S>::store(static_cast<S*>(a.dst) + off, ax, ay);
-        if (a.dog != nullptr) {
-            const float2 p = Pair<S>::load(static_cast<const S*>(a.prev) + off);
-            Pair<S>::store(static_cast<S*>(a.dog) + off, p.x - ax, p.y - ay);
-        }
-    }
+    pdl_launch_dependents();
+    pdl_wait();
+    conv_z_column<R, S, false>(a, (int64_t)blockIdx.x * Z_THREADS + threadIdx.x, blockIdx.y * Z_TZ);
 }
 
 // ---- dispatch tables over the radius -------------------------------------
@@ -188,6 +110,14 @@ template <typename Tin, bool SUB, typename Tbase, int... Rs>
 const void* xy_func_table(int r, int* smem, std::integer_sequence<int, Rs...>) {
     const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_kernel<Rs + 1, Tin, SUB, Tbase>)...};
     const int sm[] = {XYGeom<Rs + 1>::SMEM...};
+    *smem = sm[r - 1];
+    return fns[r - 1];
+}
+
+template <int TY, typename Tin, bool SUB, typename Tbase, int... Rs>
+const void* row_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, TY, Tin, SUB, Tbase>)...};
+    const int sm[] = {row_smem_bytes<Rs + 1, TY>(nx)...};
     *smem = sm[r - 1];
     return fns[r - 1];
 }
@@ -205,12 +135,38 @@ const void* xy_func(int r, int* smem) {
     return xy_func_table<Tin, SUB, Tbase>(r, smem, RadiusSeq{});
 }
 
+constexpr int ROW_TY = 16;
+
+template <typename Tin, bool SUB, typename Tbase>
+const void* row_func(int r, int nx, int* smem) {
+    return row_func_table<ROW_TY, Tin, SUB, Tbase>(r, nx, smem, RadiusSeq{});
+}
+
 }  // namespace
 
 LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const ConvXYArgs& a) {
     LaunchSpec s;
     int smem = 0;
     if (radius < 1 || radius > kMaxRadius) return s;
+    if (a.nx <= ROW_MAX_NX) {
+        if (!sub) {
+            if (src_kind == 0) s.func = row_func<float, false, float>(radius, a.nx, &smem);
+            else if (src_kind == 1) s.func = row_func<uint8_t, false, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F32) s.func = row_func<float, false, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<__half, false, float>(radius, a.nx, &smem);
+            else s.func = row_func<__nv_bfloat16, false, float>(radius, a.nx, &smem);
+        } else {
+            if (storage == SIFT3D_STORAGE_F32) s.func = row_func<float, true, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<__half, true, __half>(radius, a.nx, &smem);
+            else s.func = row_func<__nv_bfloat16, true, __nv_bfloat16>(radius, a.nx, &smem);
+        }
+        if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
+        s.block = dim3((a.nx + 31) / 32 * 32);
+        s.smem = smem;
+        s.name = sub ? "conv_xy_sub" : "conv_xy";
+        return s;
+    }
     if (!sub) {
         if (src_kind == 0) s.func = xy_func<float, false, float>(radius, &smem);
         else if (src_kind == 1) s.func = xy_func<uint8_t, false, float>(radius, &smem);
@@ -235,8 +191,7 @@ LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
     if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
     else if (storage == SIFT3D_STORAGE_F16) s.func = z_func_table<__half>(radius, RadiusSeq{});
     else s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
-    const int64_t threads = (a.pz + 1) / 2;
-    s.grid = dim3((unsigned)((threads + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
+    s.grid = dim3((unsigned)((a.pz + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
     s.block = dim3(Z_THREADS);
     s.smem = 0;
     s.name = a.dog ? "conv_z_dog" : "conv_z";

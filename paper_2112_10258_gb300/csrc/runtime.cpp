@@ -120,6 +120,13 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
         cz /= 2;
     }
     if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
+    pl.tail_start = pl.nO;
+    if (p.fuse_small_octaves)
+        for (int o = 1; o < pl.nO; ++o)
+            if (pl.oct[o].voxels() <= kTailMaxVoxels) {
+                pl.tail_start = o;
+                break;
+            }
 
     size_t off = 0;
     for (int o = 0; o < pl.nO; ++o) {
@@ -224,12 +231,11 @@ void make_pattern(const sift3d_params& p, float* out) {
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err) {
     ws->plan = plan;
     ws->capacity = capacity;
-    int n2 = 1;
-    while (n2 < capacity) n2 <<= 1;
-    ws->sort_len = capacity > 16384 ? n2 : 0;
     const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
-    const size_t keys = round_up((size_t)ws->sort_len * 8, 256);
-    ws->bytes = plan.bytes + rec + keys + 256;
+    ws->bytes = plan.bytes + rec + 256;
+    ws->tail_tasks = nullptr;
+    ws->tail_phase_begin = nullptr;
+    ws->tail_phases = 0;
     cudaError_t e = cudaMalloc(&ws->base, ws->bytes);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -244,15 +250,144 @@ int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* 
         return SIFT3D_ECUDA;
     }
     ws->staging = reinterpret_cast<sift3d_keypoint*>(ws->base + plan.bytes);
-    ws->sort_keys = ws->sort_len ? reinterpret_cast<unsigned long long*>(ws->base + plan.bytes + rec) : nullptr;
-    ws->count = reinterpret_cast<int*>(ws->base + plan.bytes + rec + keys);
+    ws->count = reinterpret_cast<int*>(ws->base + plan.bytes + rec);
     ws->count_out = ws->count + 1;
+    if (plan.tail_start < plan.nO) {
+        std::vector<TailTask> tasks;
+        std::vector<int> begin;
+        build_tail_table(*ws, &tasks, &begin);
+        const size_t tb = tasks.size() * sizeof(TailTask), pb = begin.size() * sizeof(int);
+        void* mem = nullptr;
+        e = cudaMalloc(&mem, tb + pb);
+        if (e == cudaSuccess) e = cudaMemcpy(mem, tasks.data(), tb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(static_cast<char*>(mem) + tb, begin.data(), pb, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (mem) cudaFree(mem);
+            if (err) *err = std::string("octave-tail table: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
+        }
+        ws->tail_tasks = static_cast<TailTask*>(mem);
+        ws->tail_phase_begin = reinterpret_cast<int*>(static_cast<char*>(mem) + tb);
+        ws->tail_phases = (int)begin.size() - 1;
+    }
     return SIFT3D_OK;
+}
+
+void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin) {
+    const Plan& pl = ws.plan;
+    std::vector<std::vector<TailTask>> phases;
+    auto put = [&](int ph, TailTask t) {
+        if ((int)phases.size() <= ph) phases.resize(ph + 1);
+        t.n_tiles = tail_tiles(t);
+        if (t.n_tiles > 0) phases[ph].push_back(t);
+    };
+    for (int o = pl.tail_start; o < pl.nO; ++o) {
+        const OctaveGeom& g = pl.oct[o];
+        const int off = (o - pl.tail_start) * 2 * pl.S;   // the next octave starts 2S phases later
+        auto xy_args = [&](const void* src, int64_t spy, int64_t spz, float* dst, const Taps& taps) {
+            ConvXYArgs a{};
+            a.src = src;
+            a.src_py = spy;
+            a.src_pz = spz;
+            a.src_scale = 1.0f;
+            a.dst = dst;
+            a.py = g.py;
+            a.pz = g.pz;
+            a.nx = g.nx;
+            a.ny = g.ny;
+            a.nz = g.nz;
+            a.taps = taps;
+            return a;
+        };
+        auto z_args = [&](const float* src, void* dst, const void* prev, void* dog, const Taps& taps) {
+            ConvZArgs a{};
+            a.src = src;
+            a.dst = dst;
+            a.prev = prev;
+            a.dog = dog;
+            a.py = g.py;
+            a.pz = g.pz;
+            a.nx = g.nx;
+            a.ny = g.ny;
+            a.nz = g.nz;
+            a.taps = taps;
+            return a;
+        };
+        for (int s = 1; s < pl.L; ++s) {
+            TailTask t{};
+            t.radius = pl.r_inc[s - 1];
+            if (s == 1) {
+                t.type = TailTask::XY_SUB;
+                t.xy = xy_args(ws.G(o - 1, pl.S), pl.oct[o - 1].py, pl.oct[o - 1].pz, ws.T(o), pl.t_inc[0]);
+                t.xy.base_out = ws.G(o, 0);
+            } else {
+                t.type = TailTask::XY;
+                t.xy = xy_args(ws.G(o, s - 1), g.py, g.pz, ws.T(o), pl.t_inc[s - 1]);
+            }
+            put(off + 2 * (s - 1), t);
+            TailTask z{};
+            z.type = TailTask::Z;
+            z.radius = pl.r_inc[s - 1];
+            z.z = z_args(ws.T(o), ws.G(o, s), ws.G(o, s - 1), ws.D(o, s - 1), pl.t_inc[s - 1]);
+            put(off + 2 * (s - 1) + 1, z);
+            if (pl.r_desc > 0 && s <= pl.S) {   // pre-blur of G_s for the descriptors
+                TailTask b{};
+                b.type = TailTask::XY;
+                b.radius = pl.r_desc;
+                b.xy = xy_args(ws.G(o, s), g.py, g.pz, ws.TB(o, s), pl.t_desc);
+                put(off + 2 * s, b);
+                TailTask bz{};
+                bz.type = TailTask::Z;
+                bz.radius = pl.r_desc;
+                bz.z = z_args(ws.TB(o, s), ws.B(o, s), nullptr, nullptr, pl.t_desc);
+                put(off + 2 * s + 1, bz);
+            }
+        }
+        if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
+            TailTask t{};
+            t.type = TailTask::PEAK;
+            t.pk = make_peak_args(ws, o);
+            put(off + 2 * (pl.L - 1), t);
+        }
+    }
+    tasks->clear();
+    phase_begin->assign(1, 0);
+    for (auto& ph : phases) {
+        for (auto& t : ph) tasks->push_back(t);
+        phase_begin->push_back((int)tasks->size());
+    }
 }
 
 void free_workspace(Workspace* ws) {
     if (ws->base) cudaFree(ws->base);
+    if (ws->tail_tasks) cudaFree(ws->tail_tasks);
     ws->base = nullptr;
+    ws->tail_tasks = nullptr;
+}
+
+PeakArgs make_peak_args(const Workspace& ws, int o) {
+    const Plan& pl = ws.plan;
+    const OctaveGeom& g = pl.oct[o];
+    PeakArgs pa{};
+    for (int s = 0; s < pl.nD; ++s) pa.dog[s] = ws.D(o, s);
+    pa.py = g.py;
+    pa.pz = g.pz;
+    pa.nx = g.nx;
+    pa.ny = g.ny;
+    pa.nz = g.nz;
+    pa.octave = o;
+    pa.n_scales = pl.S;
+    pa.border = pl.p.border;
+    pa.sign_sum_min = pl.p.sign_sum_min;
+    pa.contrast = (float)pl.p.contrast_thresh;
+    const double r = pl.p.curvature_r;
+    pa.curv_k1 = (float)((2.0 * r + 1.0) * (2.0 * r + 1.0) * (2.0 * r + 1.0));
+    pa.curv_k2 = (float)(r * r);
+    for (int s = 0; s < pl.L; ++s) pa.sigma_level[s] = (float)pl.sig_level[s];
+    pa.out = ws.staging;
+    pa.count = ws.count;
+    pa.capacity = ws.capacity;
+    return pa;
 }
 
 // ---- detect DAG ---------------------------------------------------------------
@@ -279,7 +414,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     std::vector<int> peak_nodes;
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
     *first_node = -1;
-    for (int o = 0; o < pl.nO; ++o) {
+    for (int o = 0; o < pl.tail_start; ++o) {
         const OctaveGeom& g = pl.oct[o];
         int prev = -1;  // node that produced G_{s-1}
         for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
@@ -355,25 +490,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         if (o > 0) g_node[o][0] = g_node[o][1];
         // peak detection on D_1..D_S
         if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
-            PeakArgs pa{};
-            for (int s = 0; s < pl.nD; ++s) pa.dog[s] = ws.D(o, s);
-            pa.py = g.py;
-            pa.pz = g.pz;
-            pa.nx = g.nx;
-            pa.ny = g.ny;
-            pa.nz = g.nz;
-            pa.octave = o;
-            pa.n_scales = pl.S;
-            pa.border = pl.p.border;
-            pa.sign_sum_min = pl.p.sign_sum_min;
-            pa.contrast = (float)pl.p.contrast_thresh;
-            const double r = pl.p.curvature_r;
-            pa.curv_k1 = (float)((2.0 * r + 1.0) * (2.0 * r + 1.0) * (2.0 * r + 1.0));
-            pa.curv_k2 = (float)(r * r);
-            for (int s = 0; s < pl.L; ++s) pa.sigma_level[s] = (float)pl.sig_level[s];
-            pa.out = ws.staging;
-            pa.count = ws.count;
-            pa.capacity = ws.capacity;
+            const PeakArgs pa = make_peak_args(ws, o);
             peak_nodes.push_back(add(peak_spec(st, pa), pa, {g_node[o][pl.L - 1]}));
             // D_1..D_S must be read in full; D_0 and D_{S+1} only around candidates
             tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
@@ -409,14 +526,25 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             }
         }
     }
+    if (pl.tail_start < pl.nO && ws.tail_tasks != nullptr) {
+        TailArgs ta{};
+        ta.tasks = ws.tail_tasks;
+        ta.phase_begin = ws.tail_phase_begin;
+        ta.n_phases = ws.tail_phases;
+        ta.bar = ws.count + 2;
+        ta.err = ws.count + 3;
+        const int tn = add(tail_spec(st, pl.S, kTailMaxCtas), ta, {g_node[pl.tail_start - 1][pl.S]});
+        nodes[tn].cooperative = true;
+        nodes[tn].label = "tail.o" + std::to_string(pl.tail_start) + "-" + std::to_string(pl.nO - 1);
+        peak_nodes.push_back(tn);
+    }
     SortArgs sa{};
     sa.staging = ws.staging;
+    sa.tail_err = ws.count + 3;
     sa.out = c.out;
     sa.count = ws.count;
     sa.count_out = ws.count_out;
     sa.capacity = ws.capacity;
-    sa.scratch_keys = ws.sort_keys;
-    sa.scratch_len = ws.sort_len;
     std::vector<int> deps = peak_nodes;
     if (deps.empty() && *first_node >= 0) deps.push_back((int)nodes.size() - 1);
     *sort_node = add(sort_spec(sa), sa, deps);
@@ -573,7 +701,9 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             Node& n = ex.nodes[i];
             if (ex.profile) cudaEventRecord(ex.ev_begin[i], st);
-            cudaError_t e = cudaLaunchKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st);
+            cudaError_t e = n.cooperative
+                                ? cudaLaunchCooperativeKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st)
+                                : cudaLaunchKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st);
             if (e != cudaSuccess) return cuda_fail(err, n.spec.name, e);
             if (ex.profile) cudaEventRecord(ex.ev_end[i], st);
         }
@@ -583,6 +713,7 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         cudaError_t e = cudaGraphCreate(&ex.graph, 0);
         if (e != cudaSuccess) return cuda_fail(err, "cudaGraphCreate", e);
         ex.gnodes.resize(ex.nodes.size());
+        const bool pdl = ws.plan.p.use_pdl != 0 && !ex.profile;
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             std::vector<cudaGraphNode_t> deps;
             for (int d : ex.nodes[i].deps) deps.push_back(ex.gnodes[d]);
@@ -593,8 +724,29 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
                 deps.assign(1, b);
             }
             cudaKernelNodeParams kp = node_params(ex.nodes[i]);
-            e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, deps.data(), deps.size(), &kp);
+            // With PDL, kernel-to-kernel edges are programmatic: the dependent
+            // launches while its predecessor drains and waits in griddepcontrol.
+            const bool prog = pdl && !ex.nodes[i].cooperative;
+            e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, prog ? nullptr : deps.data(), prog ? 0 : deps.size(),
+                                       &kp);
             if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddKernelNode", e);
+            if (prog) {
+                for (int d : ex.nodes[i].deps) {
+                    cudaGraphEdgeData ed{};
+                    if (!ex.nodes[d].cooperative) {
+                        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+                        ed.type = cudaGraphDependencyTypeProgrammatic;
+                    }
+                    e = cudaGraphAddDependencies(ex.graph, &ex.gnodes[d], &ex.gnodes[i], &ed, 1);
+                    if (e != cudaSuccess) return cuda_fail(err, "programmatic dependency", e);
+                }
+            }
+            if (ex.nodes[i].cooperative) {
+                cudaLaunchAttributeValue v{};
+                v.cooperative = 1;
+                e = cudaGraphKernelNodeSetAttribute(ex.gnodes[i], cudaLaunchAttributeCooperative, &v);
+                if (e != cudaSuccess) return cuda_fail(err, "cooperative kernel node", e);
+            }
             if (ex.profile) {
                 cudaGraphNode_t en;
                 e = cudaGraphAddEventRecordNode(&en, ex.graph, &ex.gnodes[i], 1, ex.ev_end[i]);

@@ -37,7 +37,13 @@ struct Plan {
     size_t off_TB[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
     size_t bytes = 0;
     uint64_t algo_bytes = 0;
+    int tail_start = 0;              // first octave run by the octave-tail kernel (nO: none)
 };
+
+// Octaves at or after the first o >= 1 with at most this many voxels run in
+// the octave-tail kernel when params.fuse_small_octaves is set.
+constexpr int64_t kTailMaxVoxels = 4ll << 20;
+constexpr int kTailMaxCtas = 148;
 
 // Validate params (without dims when nx <= 0) and build the plan.
 int validate_params(const sift3d_params& p, std::string* err);
@@ -51,11 +57,12 @@ struct Workspace {
     char* base = nullptr;
     size_t bytes = 0;
     sift3d_keypoint* staging = nullptr;   // unsorted records
-    int* count = nullptr;                 // running keypoint count
+    int* count = nullptr;                 // kDetectCounters ints (see common.cuh)
     int* count_out = nullptr;             // total written by the sort
-    unsigned long long* sort_keys = nullptr;
     int capacity = 0;
-    int sort_len = 0;
+    TailTask* tail_tasks = nullptr;       // device copy of the octave-tail table
+    int* tail_phase_begin = nullptr;
+    int tail_phases = 0;
     void* G(int o, int s) const { return base + plan.off_G[o][s]; }
     void* D(int o, int s) const { return base + plan.off_D[o][s]; }
     void* B(int o, int s) const {  // s = 1..S
@@ -66,6 +73,8 @@ struct Workspace {
 };
 
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
+void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin);
+PeakArgs make_peak_args(const Workspace& ws, int o);
 void free_workspace(Workspace* ws);
 
 // One kernel launch of the detect DAG with its argument bytes and dependencies.
@@ -76,6 +85,7 @@ struct Node {
     std::vector<int> deps;
     std::string label;                     // e.g. "o0.s5.conv_z_dog"
     uint64_t algo_bytes = 0;               // minimum bytes the kernel must move
+    bool cooperative = false;              // all CTAs co-resident (grid barrier inside)
     template <class A>
     void set_args(const A& a) {
         arg.assign((sizeof(A) + 7) / 8, 0ull);

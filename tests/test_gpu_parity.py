@@ -70,6 +70,7 @@ def _check_levels(S, det, ref, p):
     ((33, 17, 40), 8, 1),       # ragged in every axis, 2 octaves
     ((70, 45, 37), 16, 2),      # x spans two tiles + tail, z spans three
     ((130, 66, 20), 16, 3),     # x spans three tiles, single octave
+    ((300, 40, 22), 16, 4),     # rows wider than 256: the tiled x/y kernel with an x halo
 ])
 def test_pyramid_levels_match_oracle(S, shape, min_dim, seed):
     vol = blob_volume(seed=seed, shape=shape, n_blobs=20, sigma_range=(1.5, 4.0))
@@ -207,7 +208,7 @@ def test_constant_volume_has_no_keypoints(S):
 
 
 @pytest.mark.parametrize("shape,sigma", [((37, 29, 23), 1.2263), ((145, 174, 145), 3.09), ((70, 45, 37), 0.95),
-                                         ((130, 66, 20), 4.0)])
+                                         ((130, 66, 20), 4.0), ((301, 33, 17), 2.4525)])
 def test_gaussian_blur_matches_oracle(S, shape, sigma):
     vol = blob_volume(seed=11, shape=shape, n_blobs=15)
     det = S.Sift3D()
@@ -215,3 +216,21 @@ def test_gaussian_blur_matches_oracle(S, shape, sigma):
     ref = O.blur3d(vol, sigma)
     assert level_error(got, ref) <= REL
     det.close()
+
+
+@pytest.mark.parametrize("shape", [(145, 174, 145), (64, 64, 64), (100, 90, 80)])
+def test_octave_tail_kernel_equals_separate_launches(S, shape):
+    """Octaves after the first run in one cooperative launch by default; the
+    result must be bitwise the same as launching every pass separately."""
+    vol = brain_like_volume(seed=6, shape=shape)
+    outs = []
+    for fuse in (0, 1):
+        det, buf, n, kps = _run(S, vol, fuse_small_octaves=fuse)
+        brief, rrief = det.describe(buf, n)
+        lv = []
+        for o, dims in enumerate(S.plan(*shape)["dims"]):
+            lv.append(det.read_level(o, S.LEVEL_DOG, 2, dims).cpu().numpy().tobytes())
+            lv.append(det.read_level(o, S.LEVEL_DESC, 3, dims).cpu().numpy().tobytes())
+        outs.append((kps.tobytes(), brief[:n].cpu().numpy().tobytes(), rrief[: n * 64].cpu().numpy().tobytes(), lv))
+        det.close()
+    assert outs[0] == outs[1]
