@@ -119,8 +119,8 @@ typedef struct sift3d_params {
     int32_t  fuse_small_octaves; /* 0 = one launch per pass (default); 1 =
                                     octaves after the first (<= 4M voxels) run
                                     in one cooperative launch                  */
-    int32_t  use_pdl;            /* 1 = chain the detect graph's kernels with
-                                    programmatic dependent launch              */
+    int32_t  use_pdl;            /* 0 (default); 1 = chain the detect graph's
+                                    kernels with programmatic dependent launch */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

@@ -424,7 +424,7 @@ int sift3d_default_params(sift3d_params* out) {
     out->max_keypoints = 8192;
     out->max_inflight = 4;
     out->fuse_small_octaves = 0;
-    out->use_pdl = 1;
+    out->use_pdl = 0;
     return SIFT3D_OK;
 }
 

@@ -59,7 +59,12 @@ struct ConvXYArgs {
     void* base_out;           // sub mode: G_0 of this octave (storage type), else null
     int* zero_count;          // if set, block (0,0,0) zeroes kDetectCounters ints first
     Taps taps;
+    float* dst2;              // if set: the same plane filtered with taps2 too (the
+    Taps taps2;               //   descriptor pre-blur, radius kFusedBlurRadius)
 };
+
+// Radius of the descriptor pre-blur that the level kernels can fuse (sigma 0.95).
+constexpr int kFusedBlurRadius = 4;
 
 // Per-detect device counters: [0] keypoints found, [1] total reported by the
 // sort (-2 = a tail-kernel barrier wait ran out), [2] tail barrier, [3] tail error.
@@ -74,6 +79,9 @@ struct ConvZArgs {
     int64_t py, pz;           // shared pitches
     int nx, ny, nz;
     Taps taps;
+    const float* src2;        // if set: z pass of this second intermediate with taps2
+    void* dst2;               //   into dst2 (the pre-blurred level for the descriptors)
+    Taps taps2;
 };
 
 // ---- peak detection + compaction --------------------------------------------

@@ -32,8 +32,11 @@ __global__ void __launch_bounds__(XY_THREADS) conv_xy_kernel(const ConvXYArgs a)
     conv_xy_tile<R, Tin, SUB, Tbase>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
-template <int R, int TY, typename Tin, bool SUB, typename Tbase>
+// RB > 0: also filter the staged plane with the descriptor pre-blur (radius
+// RB <= R, taps2) into dst2, reusing the staged rows.
+template <int R, int TY, typename Tin, bool SUB, typename Tbase, int RB>
 __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
+    static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
     extern __shared__ float sm[];
     pdl_launch_dependents();
     pdl_wait();
@@ -41,6 +44,7 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
     const int WP = row_pitch(nx);
     float* in = sm;                          // (TY + 2R) x WP
     float* mid = sm + (TY + 2 * R) * WP;     // TY x WP
+    float* mid2 = mid + TY * WP;             // TY x WP (RB > 0)
     const int y0 = blockIdx.x * TY;
     const int z = blockIdx.y;
     const int c = threadIdx.x;
@@ -69,6 +73,15 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
             for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
             mid[j * WP + c] = acc;
         }
+        if constexpr (RB > 0) {
+#pragma unroll
+            for (int j = 0; j < TY; ++j) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = -RB; k <= RB; ++k) acc = fmaf(a.taps2.w[k < 0 ? -k : k], v[j + R + k], acc);
+                mid2[j * WP + c] = acc;
+            }
+        }
     }
     __syncthreads();
 
@@ -95,14 +108,29 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
         float* dst = a.dst + (int64_t)z * a.pz + (int64_t)y * a.py + x0;
         reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
         reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        if constexpr (RB > 0) {
+            float u[ROW_J + 2 * RB];
+#pragma unroll
+            for (int t = 0; t < ROW_J + 2 * RB; ++t) u[t] = mid2[r * WP + min(max(x0 - RB + t, 0), nx - 1)];
+#pragma unroll
+            for (int j = 0; j < ROW_J; ++j) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = -RB; k <= RB; ++k) acc = fmaf(a.taps2.w[k < 0 ? -k : k], u[j + RB + k], acc);
+                o[j] = acc;
+            }
+            float* dst2 = a.dst2 + (int64_t)z * a.pz + (int64_t)y * a.py + x0;
+            reinterpret_cast<float4*>(dst2)[0] = make_float4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<float4*>(dst2)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
     }
 }
 
-template <int R, typename S>
+template <int R, typename S, int RB>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
     pdl_launch_dependents();
     pdl_wait();
-    conv_z_column<R, S, false>(a, (int64_t)blockIdx.x * Z_THREADS + threadIdx.x, blockIdx.y * Z_TZ);
+    conv_z_column<R, S, false, RB>(a, (int64_t)blockIdx.x * Z_THREADS + threadIdx.x, blockIdx.y * Z_TZ);
 }
 
 // ---- dispatch tables over the radius -------------------------------------
@@ -116,17 +144,39 @@ const void* xy_func_table(int r, int* smem, std::integer_sequence<int, Rs...>) {
 
 template <int TY, typename Tin, bool SUB, typename Tbase, int... Rs>
 const void* row_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, TY, Tin, SUB, Tbase>)...};
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, TY, Tin, SUB, Tbase, 0>)...};
     const int sm[] = {row_smem_bytes<Rs + 1, TY>(nx)...};
     *smem = sm[r - 1];
     return fns[r - 1];
 }
 
+// Fused pre-blur variants exist for radii >= kFusedBlurRadius (index r-RB).
+template <int TY, typename Tin, int... Rs>
+const void* row_blur_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
+    constexpr int RB = kFusedBlurRadius;
+    const void* fns[] = {
+        reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + RB, TY, Tin, false, float, RB>)...};
+    const int sm[] = {(row_smem_bytes<Rs + RB, TY>(nx) + TY * row_pitch(nx) * 4)...};
+    if (r < RB) return nullptr;
+    *smem = sm[r - RB];
+    return fns[r - RB];
+}
+
 template <typename S, int... Rs>
 const void* z_func_table(int r, std::integer_sequence<int, Rs...>) {
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, S>)...};
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, S, 0>)...};
     return fns[r - 1];
 }
+
+template <typename S, int... Rs>
+const void* z_blur_func_table(int r, std::integer_sequence<int, Rs...>) {
+    constexpr int RB = kFusedBlurRadius;
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + RB, S, RB>)...};
+    if (r < RB) return nullptr;
+    return fns[r - RB];
+}
+
+using BlurRadiusSeq = std::make_integer_sequence<int, kMaxRadius - kFusedBlurRadius + 1>;
 
 using RadiusSeq = std::make_integer_sequence<int, kMaxRadius>;
 
@@ -148,6 +198,19 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const C
     LaunchSpec s;
     int smem = 0;
     if (radius < 1 || radius > kMaxRadius) return s;
+    if (a.dst2 != nullptr) {   // level pass with the descriptor pre-blur fused in
+        if (sub || src_kind != 2 || a.nx > ROW_MAX_NX) return s;
+        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<ROW_TY, float>(radius, a.nx, &smem, BlurRadiusSeq{});
+        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<ROW_TY, __half>(radius, a.nx, &smem, BlurRadiusSeq{});
+        else s.func = row_blur_func_table<ROW_TY, __nv_bfloat16>(radius, a.nx, &smem, BlurRadiusSeq{});
+        if (s.func == nullptr) return s;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
+        s.block = dim3((a.nx + 31) / 32 * 32);
+        s.smem = smem;
+        s.name = "conv_xy_blur";
+        return s;
+    }
     if (a.nx <= ROW_MAX_NX) {
         if (!sub) {
             if (src_kind == 0) s.func = row_func<float, false, float>(radius, a.nx, &smem);
@@ -188,13 +251,17 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const C
 LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
     LaunchSpec s;
     if (radius < 1 || radius > kMaxRadius) return s;
-    if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
+    if (a.dst2 != nullptr) {
+        if (storage == SIFT3D_STORAGE_F32) s.func = z_blur_func_table<float>(radius, BlurRadiusSeq{});
+        else if (storage == SIFT3D_STORAGE_F16) s.func = z_blur_func_table<__half>(radius, BlurRadiusSeq{});
+        else s.func = z_blur_func_table<__nv_bfloat16>(radius, BlurRadiusSeq{});
+    } else if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
     else if (storage == SIFT3D_STORAGE_F16) s.func = z_func_table<__half>(radius, RadiusSeq{});
     else s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
     s.grid = dim3((unsigned)((a.pz + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
     s.block = dim3(Z_THREADS);
     s.smem = 0;
-    s.name = a.dog ? "conv_z_dog" : "conv_z";
+    s.name = a.dst2 ? "conv_z_dog_blur" : (a.dog ? "conv_z_dog" : "conv_z");
     return s;
 }
 

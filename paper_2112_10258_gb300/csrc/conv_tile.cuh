@@ -170,7 +170,7 @@ __device__ __forceinline__ float stage_value(const ConvXYArgs& a, const Tin* src
 
 
 // Column col, planes z0 .. z0+TZ-1.
-template <int R, typename S, bool COHERENT>
+template <int R, typename S, bool COHERENT, int RB>
 __device__ __forceinline__ void conv_z_column(const ConvZArgs& a, int64_t col, int z0) {
     // Columns are addressed linearly inside a plane (pitch layout, padding
     // columns included): the z pass does not care about x/y structure.  Each
@@ -188,6 +188,15 @@ __device__ __forceinline__ void conv_z_column(const ConvZArgs& a, int64_t col, i
         const int zz = min(max(z0 - R + t, 0), a.nz - 1);
         const float* p = a.src + (int64_t)zz * a.pz + col;
         v[t] = COHERENT ? *p : __ldg(p);
+    }
+    float u[RB > 0 ? Z_TZ + 2 * RB : 1];   // second intermediate (fused pre-blur)
+    if constexpr (RB > 0) {
+#pragma unroll
+        for (int t = 0; t < Z_TZ + 2 * RB; ++t) {
+            const int zz = min(max(z0 - RB + t, 0), a.nz - 1);
+            const float* p = a.src2 + (int64_t)zz * a.pz + col;
+            u[t] = COHERENT ? *p : __ldg(p);
+        }
     }
     float pv[Z_TZ];
     if (with_dog) {
@@ -210,6 +219,12 @@ __device__ __forceinline__ void conv_z_column(const ConvZArgs& a, int64_t col, i
         const int64_t off = (int64_t)z * a.pz + col;
         dst[off] = from_f32<S>(acc);
         if (with_dog) dog[off] = from_f32<S>(pv[j] - acc);
+        if constexpr (RB > 0) {
+            float acc2 = 0.f;
+#pragma unroll
+            for (int k = -RB; k <= RB; ++k) acc2 = fmaf(a.taps2.w[k < 0 ? -k : k], u[j + RB + k], acc2);
+            static_cast<S*>(a.dst2)[off] = from_f32<S>(acc2);
+        }
     }
 }
 

@@ -413,6 +413,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     const uint64_t in_e = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 4;
     std::vector<int> peak_nodes;
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
+    bool fused[SIFT3D_MAX_OCTAVES][kMaxLevels] = {};
     *first_node = -1;
     for (int o = 0; o < pl.tail_start; ++o) {
         const OctaveGeom& g = pl.oct[o];
@@ -456,6 +457,15 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 radius = pl.r_inc[s - 1];
                 deps.push_back(prev);
             }
+            // The level's own y/x pass also applies the descriptor pre-blur to its
+            // source G_{s-1} (s-1 = 1..S) when the fused variant exists.
+            const bool fuse_blur = pl.r_desc == kFusedBlurRadius && g.nx <= 256 && !sub && src_kind == 2 &&
+                                   s - 1 >= 1 && s - 1 <= pl.S && radius >= kFusedBlurRadius;
+            if (fuse_blur) {
+                xa.dst2 = ws.TB(o, s - 1);
+                xa.taps2 = pl.t_desc;
+                fused[o][s - 1] = true;
+            }
             const int nxy = add(conv_xy_spec(radius, src_kind, st, sub, xa), xa, deps);
             if (*first_node < 0) *first_node = nxy;
             {
@@ -463,7 +473,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 // reads its source once, writes the float32 intermediate
                 // (sub-sample mode: reads 8 source voxels per voxel, also writes G_0)
                 const uint64_t rd = (o == 0 && s == 0) ? in_e * N : (sub ? 8 * e * N : e * N);
-                tag(nxy, "o%d.s%d.%s", o, s, rd + 4 * N + (sub ? e * N : 0));
+                tag(nxy, "o%d.s%d.%s", o, s, rd + 4 * N + (sub ? e * N : 0) + (xa.dst2 ? 4 * N : 0));
             }
             ConvZArgs za{};
             za.src = ws.T(o);
@@ -478,12 +488,18 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 za.prev = ws.G(o, s - 1);
                 za.dog = ws.D(o, s - 1);
             }
+            if (xa.dst2 != nullptr) {
+                za.src2 = ws.TB(o, s - 1);
+                za.dst2 = ws.B(o, s - 1);
+                za.taps2 = pl.t_desc;
+            }
             prev = add(conv_z_spec(radius, st, za), za, {nxy});
             {
                 const uint64_t N = (uint64_t)g.voxels();
                 // reads the intermediate, writes G_s; with the DoG also reads
-                // G_{s-1} and writes D_{s-1}
-                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? 2 * e * N : 0));
+                // G_{s-1} and writes D_{s-1}; with the fused pre-blur also reads
+                // its intermediate and writes the pre-blurred level
+                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? 2 * e * N : 0) + (za.dst2 ? (4 + e) * N : 0));
             }
             g_node[o][s] = prev;
         }
@@ -495,9 +511,11 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             // D_1..D_S must be read in full; D_0 and D_{S+1} only around candidates
             tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
         }
-        // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3)
+        // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3), where no level
+        // pass fused it
         if (pl.r_desc > 0) {
             for (int s = 1; s <= pl.S; ++s) {
+                if (fused[o][s]) continue;
                 ConvXYArgs xa{};
                 xa.src = ws.G(o, s);
                 xa.src_py = g.py;

@@ -171,7 +171,7 @@ __device__ __noinline__ void xy_call(const ConvXYArgs& a, int bx, int by, int z,
 }
 template <int R, typename S>
 __device__ __noinline__ void z_call(const ConvZArgs& a, int64_t col, int z0) {
-    conv_detail::conv_z_column<R, S, true>(a, col, z0);
+    conv_detail::conv_z_column<R, S, true, 0>(a, col, z0);
 }
 template <typename S>
 __device__ __noinline__ void peak_call(const PeakArgs& a, int bx, int by, int bz, float* fl, unsigned* surv, int* n) {
