@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="direct launches instead of the CUDA graph")
     ap.add_argument("--inflight", type=int, default=1,
                     help="volumes processed concurrently (separate contexts/streams, distinct inputs)")
+    ap.add_argument("--mode", choices=["headline", "batched", "serving"], default="headline",
+                    help="batched: many uneven volumes per step; serving: Poisson request stream")
+    ap.add_argument("--batch-n", type=int, default=256, help="volumes per batched step")
+    ap.add_argument("--requests", type=int, default=600, help="requests in the serving run")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving arrival rate (volumes/s)")
     return ap.parse_args()
 
 
@@ -199,6 +204,192 @@ def measured_traffic(label):
     return None
 
 
+def _dist_setup(world, local):
+    import torch
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist
+
+
+def _max_over_ranks(dist, v):
+    import torch
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- batched mode
+def run_batched(args, rank, world, local):
+    """Many volumes of uneven sizes per step (per-axis sizes uniform on
+    {96..256}, brain-like family).  All volumes are resident on the device; P
+    contexts (each with its own stream, CUDA graph per shape and one pyramid
+    arena sized for the largest shape it has seen) take the volumes round robin,
+    so the small octaves of one volume overlap the large octaves of the others.
+    The same volumes are also run through a single context one at a time (the
+    plain single-volume path) for comparison.  Weak scaling: each rank runs its
+    own batch."""
+    import torch
+    import paper_2112_10258_gb300 as S
+    from workloads.volumes import batch_volumes
+    dist = _dist_setup(world, local)
+    P = max(1, args.inflight if args.inflight > 1 else 4)
+    t_gen = time.perf_counter()
+    vols = []
+    for i, dims, v in batch_volumes(n=args.batch_n, seed=1000 * rank):
+        vols.append((dims, torch.from_numpy(v).cuda()))
+    t_gen = time.perf_counter() - t_gen
+    voxels = sum(d[0] * d[1] * d[2] for d, _ in vols)
+    streams = [torch.cuda.Stream() for _ in range(P)]
+    ctxs = [S.Sift3D(use_graphs=1) for _ in range(P)]
+    kb = [torch.empty(CAPACITY * 48, dtype=torch.uint8, device="cuda") for _ in range(P)]
+    br = [torch.empty(CAPACITY, dtype=torch.int64, device="cuda") for _ in range(P)]
+    rr = [torch.empty(CAPACITY * 64, dtype=torch.uint8, device="cuda") for _ in range(P)]
+    main_stream = torch.cuda.current_stream()
+
+    def one_pass(nctx):
+        for i, (dims, d) in enumerate(vols):
+            j = i % nctx
+            with torch.cuda.stream(streams[j]):
+                ctxs[j].detect(d, capacity=CAPACITY, out=kb[j], sync=False, stream=streams[j])
+                ctxs[j].describe(kb[j], -1, brief=br[j], rrief=rr[j], n_alloc=CAPACITY, stream=streams[j])
+
+    def timed(nctx, K):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(main_stream)
+        for st in streams[:nctx]:
+            st.wait_stream(main_stream)
+        for _ in range(K):
+            one_pass(nctx)
+        for st in streams[:nctx]:
+            main_stream.wait_stream(st)
+        e1.record(main_stream)
+        torch.cuda.synchronize()
+        return _max_over_ranks(dist, e0.elapsed_time(e1)) / K
+
+    # warm-up: every context sees its shapes once (plans, arenas, graphs)
+    for _ in range(max(1, args.warmup)):
+        one_pass(P)
+        one_pass(1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_batched = timed(P, args.steps)
+    ms_single = timed(1, args.steps)
+    clk = clocks.stop()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        n = len(vols)
+        line = {"mode": "batched", "metric": f"voxels/s over {n} uneven volumes (detect + BRIEF + RRIEF)",
+                "value": world * voxels / (ms_batched / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_batched, "ms_per_volume": ms_batched / n,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{n} brain-like volumes, per-axis sizes uniform on 96..256, cut from 4 "
+                                       f"generated 256^3 volumes", "voxels_per_step": voxels, "contexts": P,
+                           "launch": "CUDA graph per shape, P streams", "l2": "inputs larger than L2 "
+                           f"({voxels * 4 >> 20} MiB resident)", "host_generation_s": round(t_gen, 1)},
+                "single_volume_path": {"value": world * voxels / (ms_single / 1e3), "unit": UNIT,
+                                       "ms_per_step": ms_single, "ms_per_volume": ms_single / n,
+                                       "note": "same volumes, one context, one at a time"},
+                "speedup_vs_single": ms_single / ms_batched, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- serving mode
+def run_serving(args, rank, world, local):
+    """A Poisson request stream (default 200 volumes/s) of uint8 volumes, sizes
+    64^3, 145x174x145 and 256x256x192 with equal probability, through
+    sift3d_submit / sift3d_poll (admission by a 40 GB device budget, detect and
+    describe per request, results copied back to the host).  Latency is the
+    library's own submit -> results-ready time.  Weak scaling: each rank serves
+    its own stream."""
+    import torch
+    import paper_2112_10258_gb300 as S
+    from workloads.volumes import SERVING_SHAPES, brain_like_volume, poisson_arrivals, to_uint8
+    dist = _dist_setup(world, local)
+    pool = {}
+    for k, shp in enumerate(SERVING_SHAPES):
+        pool[shp] = [torch.from_numpy(to_uint8(brain_like_volume(seed=100 * rank + 10 * k + j, shape=shp))
+                                      ).pin_memory() for j in range(2)]
+    arrivals = poisson_arrivals(args.requests, rate_per_s=args.rate, seed=rank)
+    srv = S.Sift3D(max_inflight=8, max_keypoints=8192, hbm_budget_bytes=40 << 30)
+
+    def drive(reqs):
+        out = {}
+        pending = {}
+        t0 = time.perf_counter()
+        deadline = t0 + 60.0 + (reqs[-1][0] if reqs else 0.0)
+        for i, (t_arr, shp) in enumerate(reqs):
+            while True:
+                now = time.perf_counter() - t0
+                for t in list(pending):
+                    r = srv.poll(t, 0, copy=False)
+                    if r is not None:
+                        out[pending.pop(t)] = r
+                        srv.release(t)
+                if now >= t_arr:
+                    break
+                time.sleep(min(2e-4, t_arr - now))
+            h = pool[shp][i % 2]
+            pending[srv.submit_ptr(h.data_ptr(), S.DTYPE_U8, shp, flags=S.SUBMIT_NOCOPY)] = i
+        while pending:
+            if time.perf_counter() > deadline:
+                raise RuntimeError("serving requests did not finish in time")
+            for t in list(pending):
+                r = srv.poll(t, 200, copy=False)
+                if r is not None:
+                    out[pending.pop(t)] = r
+                    srv.release(t)
+        return out, time.perf_counter() - t0
+
+    drive(poisson_arrivals(max(24, 8 * args.warmup), rate_per_s=args.rate, seed=10_000 + rank))  # warm-up
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    res, wall = drive(arrivals)
+    clk = clocks.stop()
+    srv.close()
+    lat = np.array([res[i]["latency_ms"] for i in range(len(arrivals))])
+    que = np.array([res[i]["queue_ms"] for i in range(len(arrivals))])
+    kps = np.array([res[i]["n_needed"] for i in range(len(arrivals))])
+    by_shape = {}
+    for i, (_, shp) in enumerate(arrivals):
+        by_shape.setdefault("x".join(map(str, shp)), []).append(lat[i])
+    vps = len(arrivals) / wall
+    vps = _max_over_ranks(dist, -vps) if dist is not None else vps
+    if rank == 0:
+        line = {"mode": "serving", "metric": "serving p50/p99 latency (ms) and volumes/s, Poisson arrivals",
+                "value": float(np.percentile(lat, 50)), "unit": "ms (p50)", "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "queue_p99_ms": float(np.percentile(que, 99)), "volumes_per_s": abs(vps) * world,
+                "offered_rate_per_s": args.rate, "requests": len(arrivals), "n_gpus": world,
+                "higher_is_better": False, "scaling": "weak", "dtype": "u8 input, f32 pyramid",
+                "data": "synthetic",
+                "per_shape_p50_p99_ms": {k: [float(np.percentile(v, 50)), float(np.percentile(v, 99))]
+                                         for k, v in by_shape.items()},
+                "keypoints_mean": float(kps.mean()),
+                "config": {"workload": "Poisson arrivals, sizes 64^3 / 145x174x145 / 256x256x192 equally likely, "
+                                       "uint8 brain-like volumes in pinned host memory", "budget_gb": 40,
+                           "max_inflight": 8, "api": "sift3d_submit(NOCOPY) / sift3d_poll; results read on host"},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -216,6 +407,12 @@ def main():
     from workloads.volumes import brain_like_volume
 
     torch.cuda.set_device(local)
+    if args.mode == "batched":
+        run_batched(args, rank, world, local)
+        return
+    if args.mode == "serving":
+        run_serving(args, rank, world, local)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -52,6 +52,8 @@ struct sift3d_ctx {
     std::mutex err_mu;
     float* blur_scratch = nullptr;     // two pitched float32 volumes
     int64_t blur_scratch_elems = 0;    // per volume
+    char* arena = nullptr;             // device memory every cached shape's pyramid uses
+    size_t arena_bytes = 0;
 };
 
 namespace {
@@ -74,6 +76,10 @@ int ensure_device(sift3d_ctx* c) {
 }
 
 int get_entry(sift3d_ctx* c, int nx, int ny, int nz, int dtype, int capacity, DetectEntry** out) {
+    // Every shape's pyramid lives in one context arena (a context runs one
+    // detect at a time, and a pyramid only has to last until the next detect);
+    // each shape keeps its own plan and graph.  The arena grows to the largest
+    // shape seen; growing it drops the cached graphs, which point into it.
     const ShapeKey key{nx, ny, nz, capacity};
     auto it = c->cache.find(key);
     if (it == c->cache.end()) {
@@ -81,8 +87,20 @@ int get_entry(sift3d_ctx* c, int nx, int ny, int nz, int dtype, int capacity, De
         std::string err;
         int rc = make_plan(c->p, nx, ny, nz, dtype, &pl, &err);
         if (rc != SIFT3D_OK) return set_err(c, rc, err);
+        const size_t need = workspace_bytes(pl, capacity);
+        if (need > c->arena_bytes) {
+            cudaDeviceSynchronize();
+            c->cache.clear();
+            c->last = nullptr;
+            if (c->arena) cudaFree(c->arena);
+            c->arena = nullptr;
+            c->arena_bytes = 0;
+            rc = alloc_device_zeroed(need, &c->arena, &err);
+            if (rc != SIFT3D_OK) return set_err(c, rc, err);
+            c->arena_bytes = need;
+        }
         auto ent = std::make_unique<DetectEntry>();
-        rc = alloc_workspace(pl, capacity, &ent->ws, &err);
+        rc = bind_workspace(pl, capacity, c->arena, &ent->ws, &err);
         if (rc != SIFT3D_OK) return set_err(c, rc, err);
         it = c->cache.emplace(key, std::move(ent)).first;
     }
@@ -464,6 +482,7 @@ void sift3d_destroy(sift3d_ctx* ctx) {
     ctx->server.reset();
     if (ctx->device >= 0) cudaDeviceSynchronize();
     ctx->cache.clear();
+    if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
     delete ctx;
 }

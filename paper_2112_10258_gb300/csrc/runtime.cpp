@@ -228,27 +228,20 @@ void make_pattern(const sift3d_params& p, float* out) {
 }
 
 // ---- workspaces -------------------------------------------------------------
-int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err) {
+size_t workspace_bytes(const Plan& plan, int capacity) {
+    const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
+    return plan.bytes + rec + 256;
+}
+
+int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, std::string* err) {
     ws->plan = plan;
     ws->capacity = capacity;
-    const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
-    ws->bytes = plan.bytes + rec + 256;
+    ws->base = base;
+    ws->bytes = workspace_bytes(plan, capacity);
     ws->tail_tasks = nullptr;
     ws->tail_phase_begin = nullptr;
     ws->tail_phases = 0;
-    cudaError_t e = cudaMalloc(&ws->base, ws->bytes);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        ws->base = nullptr;
-        if (err) *err = std::string("cudaMalloc of the workspace failed: ") + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
-    }
-    // Padding columns are read (never used) by the column-linear z pass.
-    e = cudaMemset(ws->base, 0, ws->bytes);
-    if (e != cudaSuccess) {
-        if (err) *err = std::string("cudaMemset failed: ") + cudaGetErrorString(e);
-        return SIFT3D_ECUDA;
-    }
+    const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
     ws->staging = reinterpret_cast<sift3d_keypoint*>(ws->base + plan.bytes);
     ws->count = reinterpret_cast<int*>(ws->base + plan.bytes + rec);
     ws->count_out = ws->count + 1;
@@ -258,11 +251,12 @@ int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* 
         build_tail_table(*ws, &tasks, &begin);
         const size_t tb = tasks.size() * sizeof(TailTask), pb = begin.size() * sizeof(int);
         void* mem = nullptr;
-        e = cudaMalloc(&mem, tb + pb);
+        cudaError_t e = cudaMalloc(&mem, tb + pb);
         if (e == cudaSuccess) e = cudaMemcpy(mem, tasks.data(), tb, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(static_cast<char*>(mem) + tb, begin.data(), pb, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             if (mem) cudaFree(mem);
+            (void)cudaGetLastError();
             if (err) *err = std::string("octave-tail table: ") + cudaGetErrorString(e);
             return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
         }
@@ -271,6 +265,36 @@ int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* 
         ws->tail_phases = (int)begin.size() - 1;
     }
     return SIFT3D_OK;
+}
+
+int alloc_device_zeroed(size_t bytes, char** out, std::string* err) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, bytes);   // padding columns start finite
+    if (e != cudaSuccess) {
+        if (p) cudaFree(p);
+        (void)cudaGetLastError();
+        if (err) *err = std::string("device allocation of the workspace failed: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
+    }
+    *out = static_cast<char*>(p);
+    return SIFT3D_OK;
+}
+
+int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err) {
+    char* base = nullptr;
+    int rc = alloc_device_zeroed(workspace_bytes(plan, capacity), &base, err);
+    if (rc != SIFT3D_OK) return rc;
+    rc = bind_workspace(plan, capacity, base, ws, err);
+    ws->owns_base = true;
+    return rc;
+}
+
+void free_workspace(Workspace* ws) {
+    if (ws->base && ws->owns_base) cudaFree(ws->base);
+    if (ws->tail_tasks) cudaFree(ws->tail_tasks);
+    ws->base = nullptr;
+    ws->tail_tasks = nullptr;
 }
 
 void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin) {
@@ -358,12 +382,6 @@ void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::ve
     }
 }
 
-void free_workspace(Workspace* ws) {
-    if (ws->base) cudaFree(ws->base);
-    if (ws->tail_tasks) cudaFree(ws->tail_tasks);
-    ws->base = nullptr;
-    ws->tail_tasks = nullptr;
-}
 
 PeakArgs make_peak_args(const Workspace& ws, int o) {
     const Plan& pl = ws.plan;

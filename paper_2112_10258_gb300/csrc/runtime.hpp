@@ -56,6 +56,7 @@ struct Workspace {
     Plan plan;
     char* base = nullptr;
     size_t bytes = 0;
+    bool owns_base = false;               // false: base lives in a context arena
     sift3d_keypoint* staging = nullptr;   // unsorted records
     int* count = nullptr;                 // kDetectCounters ints (see common.cuh)
     int* count_out = nullptr;             // total written by the sort
@@ -72,6 +73,9 @@ struct Workspace {
     float* TB(int o, int s) const { return reinterpret_cast<float*>(base + plan.off_TB[o][s - 1]); }
 };
 
+size_t workspace_bytes(const Plan& plan, int capacity);
+int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, std::string* err);
+int alloc_device_zeroed(size_t bytes, char** out, std::string* err);
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
 void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin);
 PeakArgs make_peak_args(const Workspace& ws, int o);

@@ -234,3 +234,24 @@ def test_octave_tail_kernel_equals_separate_launches(S, shape):
         outs.append((kps.tobytes(), brief[:n].cpu().numpy().tobytes(), rrief[: n * 64].cpu().numpy().tobytes(), lv))
         det.close()
     assert outs[0] == outs[1]
+
+
+def test_one_context_many_shapes_shares_its_arena(S):
+    """A context keeps one device arena for the pyramids of every shape it has
+    seen; growing it (a larger volume after smaller ones) and going back to a
+    cached smaller shape must give the results a fresh context gives."""
+    shapes = [(40, 36, 34), (96, 120, 100), (64, 64, 64), (40, 36, 34), (150, 97, 111)]
+    vols = [brain_like_volume(seed=20 + i, shape=s) for i, s in enumerate(shapes)]
+    shared = S.Sift3D()
+    for vol, shape in zip(vols, shapes):
+        got = []
+        for det in (shared, S.Sift3D()):
+            buf, n = det.detect(torch.from_numpy(vol).cuda(), capacity=8192)
+            brief, rrief = det.describe(buf, n)
+            lvl = det.read_level(0, S.LEVEL_DOG, 1, shape).cpu().numpy()
+            got.append((S.keypoints_to_numpy(buf, n).tobytes(), brief[:n].cpu().numpy().tobytes(),
+                        rrief[: n * 64].cpu().numpy().tobytes(), lvl.tobytes()))
+            if det is not shared:
+                det.close()
+        assert got[0] == got[1], f"shape {shape}"
+    shared.close()

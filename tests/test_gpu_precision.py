@@ -1,0 +1,60 @@
+"""Pyramid levels stored in FP16 / BF16 (arithmetic in FP32): keypoint recall and
+precision and descriptor agreement against the FP64 oracle on brain-like
+145x174x145 volumes.  The full 16-seed report is bench.py --precision-report;
+these tests hold the floors on two seeds."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sift3d_oracle as O  # noqa: E402
+from tests.precision import descriptor_agreement, match_keypoints  # noqa: E402
+from workloads.volumes import brain_like_volume  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2112_10258_gb300 as S
+    return S
+
+
+@pytest.fixture(scope="module")
+def refs():
+    out = {}
+    p = O.Params()
+    for seed in (0, 1):
+        vol = brain_like_volume(seed=seed)
+        r = O.detect(vol, p)
+        d = O.describe(r.pyramid, r.keypoints, p)
+        out[seed] = (vol, r, d)
+    return out
+
+
+@pytest.mark.parametrize("storage,name,level_tol,min_recall,min_bits", [
+    (1, "f16", 2e-3, 0.90, 0.97),
+    (2, "bf16", 1.5e-2, 0.60, 0.90),
+])
+def test_reduced_precision_storage(S, refs, storage, name, level_tol, min_recall, min_bits):
+    for seed, (vol, ref, dref) in refs.items():
+        det = S.Sift3D(storage=storage)
+        buf, n = det.detect(torch.from_numpy(vol).cuda(), capacity=16384)
+        kps = S.keypoints_to_numpy(buf, n)
+        brief, rrief = det.describe(buf, n)
+        b = brief[:n].cpu().numpy().view(np.uint64)
+        r = rrief[: n * 64].cpu().numpy().reshape(n, 64)
+        pairs, recall, precision = match_keypoints(kps, ref.keypoints)
+        bits, ranks = descriptor_agreement(b, r, dref.brief, dref.rrief, pairs)
+        g = det.read_level(0, S.LEVEL_GAUSS, 3, (145, 174, 145)).cpu().numpy()
+        o = ref.pyramid.G[0][3]
+        err = float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+        print(f"{name} seed {seed}: kp {n}/{ref.keypoints.size} recall {recall:.4f} precision {precision:.4f} "
+              f"bits {bits:.4f} ranks {ranks:.4f} G3 err {err:.2e}")
+        assert err <= level_tol
+        assert recall >= min_recall and precision >= min_recall
+        assert bits >= min_bits
+        det.close()

@@ -137,3 +137,23 @@ def poisson_arrivals(n: int, rate_per_s: float = 200.0, seed: int = 0,
     t = np.cumsum(gaps) - gaps[0]
     idx = rng.integers(0, len(shapes), size=n)
     return [(float(t[i]), tuple(shapes[idx[i]])) for i in range(n)]
+
+
+def batch_volumes(n: int = 256, lo: int = 96, hi: int = 256, n_bases: int = 4, seed: int = 0):
+    """``n`` volumes of the brain-like family with per-axis sizes on {lo..hi}.
+
+    Generating hundreds of brain-like volumes one by one takes minutes of host
+    time, so ``n_bases`` hi^3 volumes are generated (seeds seed .. seed+n_bases-1)
+    and volume i is a box of shape ``batch_shapes(n, lo, hi, seed)[i]`` cut from
+    base i % n_bases at an offset drawn uniformly from the positions where it
+    fits.  Yields (i, (nx, ny, nz), contiguous float32 array) lazily, so callers
+    can upload each volume and drop the host copy.
+    """
+    shapes = batch_shapes(n, lo, hi, seed)
+    bases = [brain_like_volume(seed=seed + b, shape=(hi, hi, hi)) for b in range(n_bases)]
+    rng = np.random.default_rng(seed + 1_000_003)
+    for i, (nx, ny, nz) in enumerate(shapes):
+        ox = int(rng.integers(0, hi - nx + 1))
+        oy = int(rng.integers(0, hi - ny + 1))
+        oz = int(rng.integers(0, hi - nz + 1))
+        yield i, (nx, ny, nz), np.ascontiguousarray(bases[i % n_bases][oz:oz + nz, oy:oy + ny, ox:ox + nx])
