@@ -292,6 +292,15 @@ int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index,
 int sift3d_stage_times(sift3d_ctx* ctx, int max, float* ms_out, const char** names_out,
                        uint64_t* algo_bytes_out, int* n_out);
 
+/* Timeline of the last profiled detect (no counterpart in the paper): for each
+ * kernel, in the order of sift3d_stage_times, the times in ms of its begin and
+ * end events relative to the begin event of the first kernel (the root of the
+ * detect graph).  Kernels on concurrent octave branches overlap in time.
+ *   begin_ms_out, end_ms_out  host arrays of max floats (caller owned).
+ *   n_out    receives the number of kernels (may exceed max).
+ * Errors: SIFT3D_EINVAL (no prior detect or profiling off), SIFT3D_ECUDA. */
+int sift3d_stage_timeline(sift3d_ctx* ctx, int max, float* begin_ms_out, float* end_ms_out, int* n_out);
+
 /* Serving (no counterpart in the paper).  sift3d_submit copies a HOST volume
  * (the library reads it before returning, unless flags has
  * SIFT3D_SUBMIT_NOCOPY) into a request and queues it; the

@@ -101,6 +101,8 @@ SIGNATURES = {
                                                C.c_void_p, C.c_void_p]),
     "sift3d_stage_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_char_p),
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
+    "sift3d_stage_timeline": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                        C.POINTER(C.c_int)]),
 }
 
 
@@ -218,3 +220,16 @@ def sift3d_stage_times(ctx, max_n: int = 512):
         return rc, []
     k = min(n.value, max_n)
     return rc, [(names[i].decode(), float(ms[i]), int(ab[i])) for i in range(k)]
+
+
+def sift3d_stage_timeline(ctx, max_n: int = 512):
+    """Returns (rc, [(begin_ms, end_ms), ...]) for the last profiled detect,
+    relative to the first kernel's begin; same order as sift3d_stage_times."""
+    b = (C.c_float * max_n)()
+    e = (C.c_float * max_n)()
+    n = C.c_int(0)
+    rc = _lib.sift3d_stage_timeline(C.c_void_p(ctx), max_n, b, e, C.byref(n))
+    if rc != OK:
+        return rc, []
+    k = min(n.value, max_n)
+    return rc, [(float(b[i]), float(e[i])) for i in range(k)]

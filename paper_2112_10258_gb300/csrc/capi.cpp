@@ -514,7 +514,7 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
         cudaError_t e = cudaMemcpyAsync(&h, ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("detect: ") + cudaGetErrorString(e));
-        if (h == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "octave-tail barrier wait ran out");
+        if (h == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "a bounded device wait ran out (octave-tail barrier or peak tile load)");
         *n_out = h;
         if (h > capacity) return set_err(ctx, SIFT3D_ECAPACITY, "more keypoints than capacity");
     }
@@ -616,6 +616,27 @@ int sift3d_stage_times(sift3d_ctx* ctx, int max, float* ms_out, const char** nam
         ms_out[i] = ms;
         if (names_out) names_out[i] = ex.nodes[i].label.c_str();
         if (algo_bytes_out) algo_bytes_out[i] = ex.nodes[i].algo_bytes;
+    }
+    return SIFT3D_OK;
+}
+
+int sift3d_stage_timeline(sift3d_ctx* ctx, int max, float* begin_ms_out, float* end_ms_out, int* n_out) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->last || !ctx->last->ex[ctx->last_dtype]) return set_err(ctx, SIFT3D_EINVAL, "no prior detect");
+    const DetectExec& ex = *ctx->last->ex[ctx->last_dtype];
+    if (!ex.profile || ex.ev_end.empty()) return set_err(ctx, SIFT3D_EINVAL, "context created with profile = 0");
+    if (max < 0 || (max > 0 && (!begin_ms_out || !end_ms_out))) return set_err(ctx, SIFT3D_EINVAL, "bad output array");
+    const int n = (int)ex.nodes.size();
+    if (n_out) *n_out = n;
+    for (int i = 0; i < n && i < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(ex.ev_end[i]);
+        float b = 0.f, t = 0.f;
+        // node 0 is the first pass of octave 0, the root of the DAG
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ex.ev_begin[0], ex.ev_begin[i]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ex.ev_begin[0], ex.ev_end[i]);
+        if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("stage_timeline: ") + cudaGetErrorString(e));
+        begin_ms_out[i] = b;
+        end_ms_out[i] = t;
     }
     return SIFT3D_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the sm_103a kernels and the host runtime.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -97,6 +98,20 @@ struct PeakArgs {
     int capacity;
 };
 
+// Arguments of the TMA-fed peak kernel: the octave's DoG levels D_0..D_{S+1}
+// lie at a constant stride in the workspace and are described by one 4D tensor
+// map (x, y, z, level), passed as a __grid_constant__ kernel parameter.
+struct PeakTmaArgs {   // 128-byte aligned through CUtensorMap
+    CUtensorMap dogs;
+    PeakArgs a;
+    int x_start;                        // x of the first tile's halo origin (multiple of 8)
+    int* err;                           // set to 1 when a TMA wait runs out
+};
+
+// Tile geometry of the peak kernel for a storage type: the halo origin of the
+// first x tile and the TMA box (x, y, z) of one level.
+void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z);
+
 // ---- canonical sort of the staging records into the caller's array --------
 struct SortArgs {
     const sift3d_keypoint* staging;
@@ -168,7 +183,7 @@ struct LaunchSpec {
 // `src_kind` for conv_xy is 0 = float32, 1 = uint8, 2 = storage type.
 LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const ConvXYArgs& a);
 LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a);
-LaunchSpec peak_spec(int storage, const PeakArgs& a);
+LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);

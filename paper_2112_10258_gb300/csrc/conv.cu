@@ -8,6 +8,9 @@
 //            In sub-sample mode the staged values are the 2x2x2 means of the
 //            previous octave's level S (Sec. 2.2.2 "Sub-sampling"), and the
 //            tile's own means are written out as the octave's G_0.
+//   conv_xy_row  (rows up to 256 wide) one CTA per 16 full rows of a plane,
+//            column pairs in the y pass and row pairs in the x pass, each tap
+//            one paired FP32 FMA (see below).
 //   conv_z   one thread per two adjacent columns and TZ outputs along z: the
 //            TZ + 2R inputs are loaded into registers (clamped z) and the TZ
 //            outputs accumulate from registers.  The epilogue stores G_s and the
@@ -32,97 +35,43 @@ __global__ void __launch_bounds__(XY_THREADS) conv_xy_kernel(const ConvXYArgs a)
     conv_xy_tile<R, Tin, SUB, Tbase>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
-// RB > 0: also filter the staged plane with the descriptor pre-blur (radius
-// RB <= R, taps2) into dst2, reusing the staged rows.
-template <int R, int TY, typename Tin, bool SUB, typename Tbase, int RB>
-__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
-    static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
-    extern __shared__ float sm[];
-    pdl_launch_dependents();
-    pdl_wait();
-    const int nx = a.nx;
-    const int WP = row_pitch(nx);
-    float* in = sm;                          // (TY + 2R) x WP
-    float* mid = sm + (TY + 2 * R) * WP;     // TY x WP
-    float* mid2 = mid + TY * WP;             // TY x WP (RB > 0)
-    const int y0 = blockIdx.x * TY;
-    const int z = blockIdx.y;
-    const int c = threadIdx.x;
-    const Tin* src = static_cast<const Tin*>(a.src);
-    if (a.zero_count != nullptr && y0 == 0 && z == 0 && c < kDetectCounters) a.zero_count[c] = 0;
+// ---- z pass on column pairs with paired FP32 FMAs ---------------------------
+// A thread owns two adjacent columns (pitched rows hold a multiple of 8
+// elements, so a pair never straddles a row) and TZ outputs along z.  Loads and
+// stores move both columns at once, and each tap is one __ffma2_rn for the
+// pair: per column this is exactly the scalar chain acc = fmaf(w_|k|, in, acc)
+// in ascending k, so results are bitwise those of a one-column-per-thread pass.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 get(T v) { return v; }
+    static __device__ __forceinline__ T put(float2 v) { return v; }
+};
+template <> struct Pair<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ float2 get(T v) { return __half22float2(v); }
+    static __device__ __forceinline__ T put(float2 v) { return __floats2half2_rn(v.x, v.y); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ float2 get(T v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ T put(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
+};
 
-    if (c < nx) {
-        float v[TY + 2 * R];
-#pragma unroll
-        for (int r = 0; r < TY + 2 * R; ++r) {
-            const int gy = min(max(y0 - R + r, 0), a.ny - 1);
-            v[r] = stage_value<Tin, SUB>(a, src, z, gy, c);
-        }
-        if constexpr (SUB) {   // this CTA's own rows of the sub-sampled level are G_0
-#pragma unroll
-            for (int r = 0; r < TY; ++r)
-                if (y0 + r < a.ny)
-                    static_cast<Tbase*>(a.base_out)[(int64_t)z * a.pz + (int64_t)(y0 + r) * a.py + c] =
-                        from_f32<Tbase>(v[R + r]);
-        }
-        // y pass straight from the register window
-#pragma unroll
-        for (int j = 0; j < TY; ++j) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
-            mid[j * WP + c] = acc;
-        }
-        if constexpr (RB > 0) {
-#pragma unroll
-            for (int j = 0; j < TY; ++j) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = -RB; k <= RB; ++k) acc = fmaf(a.taps2.w[k < 0 ? -k : k], v[j + R + k], acc);
-                mid2[j * WP + c] = acc;
-            }
-        }
-    }
-    __syncthreads();
+__device__ __forceinline__ float2 f2(float w) { return make_float2(w, w); }
 
-    // x pass: item = (row r, group g of 8 columns), r fastest so a warp's lanes
-    // read different rows (odd pitch: no bank conflicts)
-    const int groups = (nx + ROW_J - 1) / ROW_J;
-    for (int item = threadIdx.x; item < TY * groups; item += blockDim.x) {
-        const int r = item % TY;
-        const int g = item / TY;
-        const int y = y0 + r;
-        if (y >= a.ny) continue;
-        const int x0 = g * ROW_J;
-        float v[ROW_J + 2 * R];
+// Loads the TZ + 2R inputs of a column pair, z clamped to [0, nz-1]; the
+// branch on `interior` is uniform over the CTA.
+template <int N, int R>
+__device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, int z0, int nz, bool interior,
+                                              float2 (&v)[N]) {
+    if (interior) {
+        const float2* p = src + (int64_t)(z0 - R) * pz2;
 #pragma unroll
-        for (int t = 0; t < ROW_J + 2 * R; ++t) v[t] = mid[r * WP + min(max(x0 - R + t, 0), nx - 1)];
-        float o[ROW_J];
+        for (int t = 0; t < N; ++t) v[t] = __ldg(p + t * pz2);
+    } else {
 #pragma unroll
-        for (int j = 0; j < ROW_J; ++j) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
-            o[j] = acc;
-        }
-        float* dst = a.dst + (int64_t)z * a.pz + (int64_t)y * a.py + x0;
-        reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
-        reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
-        if constexpr (RB > 0) {
-            float u[ROW_J + 2 * RB];
-#pragma unroll
-            for (int t = 0; t < ROW_J + 2 * RB; ++t) u[t] = mid2[r * WP + min(max(x0 - RB + t, 0), nx - 1)];
-#pragma unroll
-            for (int j = 0; j < ROW_J; ++j) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = -RB; k <= RB; ++k) acc = fmaf(a.taps2.w[k < 0 ? -k : k], u[j + RB + k], acc);
-                o[j] = acc;
-            }
-            float* dst2 = a.dst2 + (int64_t)z * a.pz + (int64_t)y * a.py + x0;
-            reinterpret_cast<float4*>(dst2)[0] = make_float4(o[0], o[1], o[2], o[3]);
-            reinterpret_cast<float4*>(dst2)[1] = make_float4(o[4], o[5], o[6], o[7]);
-        }
+        for (int t = 0; t < N; ++t) v[t] = __ldg(src + (int64_t)min(max(z0 - R + t, 0), nz - 1) * pz2);
     }
 }
 
@@ -130,7 +79,248 @@ template <int R, typename S, int RB>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
     pdl_launch_dependents();
     pdl_wait();
-    conv_z_column<R, S, false, RB>(a, (int64_t)blockIdx.x * Z_THREADS + threadIdx.x, blockIdx.y * Z_TZ);
+    using P = Pair<S>;
+    using PT = typename P::T;
+    const int64_t pair = (int64_t)blockIdx.x * Z_THREADS + threadIdx.x;
+    const int64_t pz2 = a.pz / 2;
+    if (pair >= pz2) return;
+    const int z0 = blockIdx.y * Z_TZ;
+    const bool interior = z0 - R >= 0 && z0 + Z_TZ + R <= a.nz;
+    const bool with_dog = a.dog != nullptr;
+    float2 v[Z_TZ + 2 * R];
+    load_z_window<Z_TZ + 2 * R, R>(reinterpret_cast<const float2*>(a.src) + pair, pz2, z0, a.nz, interior, v);
+    float2 pv[Z_TZ];
+    const PT* prev = static_cast<const PT*>(a.prev) + pair;
+    if (with_dog) {
+#pragma unroll
+        for (int j = 0; j < Z_TZ; ++j) pv[j] = P::get(prev[(int64_t)min(z0 + j, a.nz - 1) * pz2]);
+    }
+    PT* dst = static_cast<PT*>(a.dst) + pair;
+    PT* dog = static_cast<PT*>(a.dog) + pair;
+#pragma unroll
+    for (int j = 0; j < Z_TZ; ++j) {
+        const int z = z0 + j;
+        if (z >= a.nz) break;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(a.taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
+        const int64_t off = (int64_t)z * pz2;
+        dst[off] = P::put(acc);
+        if (with_dog) dog[off] = P::put(make_float2(pv[j].x - acc.x, pv[j].y - acc.y));
+    }
+    if constexpr (RB > 0) {   // the fused descriptor pre-blur, after the level so registers are reused
+        float2 u[Z_TZ + 2 * RB];
+        load_z_window<Z_TZ + 2 * RB, RB>(reinterpret_cast<const float2*>(a.src2) + pair, pz2, z0, a.nz,
+                                         z0 - RB >= 0 && z0 + Z_TZ + RB <= a.nz, u);
+        PT* dst2 = static_cast<PT*>(a.dst2) + pair;
+#pragma unroll
+        for (int j = 0; j < Z_TZ; ++j) {
+            if (z0 + j >= a.nz) break;
+            float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = -RB; k <= RB; ++k) acc2 = __ffma2_rn(f2(a.taps2.w[k < 0 ? -k : k]), u[j + RB + k], acc2);
+            dst2[(int64_t)(z0 + j) * pz2] = P::put(acc2);
+        }
+    }
+}
+
+// ---- y/x pass of full rows (nx <= 256) with paired FP32 FMAs -----------------
+// One CTA filters rows y0 .. y0+15 of one plane, full width.
+//   y pass: a task owns a column pair and 8 output rows; it loads the 8 + 2R
+//           source rows (clamped y) into registers and filters both columns at
+//           once with __ffma2_rn.  Results go to shared memory as row pairs:
+//           element [rp][c] holds (row 2rp, row 2rp+1) of column c, so the x
+//           pass reads two rows with one 8-byte access.
+//   aprons: each row-pair line carries RA = R + (R & 1) copies of column 0 on
+//           the left and copies of column nx-1 on the right, which is the
+//           clamp-to-edge border: the x pass reads without index clamps.
+//   x pass: a task owns a row pair and 8 output columns; it reads its window
+//           with 16-byte shared loads and filters both rows at once.
+// Per column and row every output is the scalar chain fmaf(w_|k|, in, acc) in
+// ascending k, so the pairing changes no result bit.
+// MODE 0: source is a pitched pyramid level (storage type Tin), read in pairs;
+// MODE 1: source is the caller's dense volume (float32 or uint8, row pitch nx);
+// MODE 2: source is the previous octave's level S, each value the 2x2x2 mean
+//         (Sec. 2.2.2 "Sub-sampling"), and the CTA's own rows of the means are
+//         written to base_out as the octave's G_0.
+constexpr int RY = 8;                 // rows per y task
+constexpr int ROW_TY = 2 * RY;        // rows per CTA
+
+__host__ __device__ constexpr int row_apron(int R) { return R + (R & 1); }
+
+// Row-pair line length in float2: window reads stay inside, and it is 2 mod 4
+// so that 8 lanes reading 8 different lines at one column hit 8 distinct
+// 16-byte bank groups.
+__host__ __device__ constexpr int row_line(int nx, int R) {
+    const int w = 8 * ((nx + 7) / 8) + 2 * R + 4;
+    return w + ((2 - (w & 3)) & 3);
+}
+
+__host__ __device__ constexpr int row_smem(int nx, int R, int RB) {
+    return (RB > 0 ? 2 : 1) * (ROW_TY / 2) * row_line(nx, R) * 8;
+}
+
+__host__ __device__ constexpr int row_threads(int nx) {
+    const int pairs = (nx + 1) / 2, groups = (nx + 7) / 8;
+    const int t = 2 * pairs > 8 * groups ? 2 * pairs : 8 * groups;
+    return (t + 31) / 32 * 32;
+}
+
+template <typename Tin>
+__device__ __forceinline__ float sub_mean(const Tin* p, int64_t py, int64_t pz) {
+    float acc = 0.f;
+    acc += load_f(p);
+    acc += load_f(p + 1);
+    acc += load_f(p + py);
+    acc += load_f(p + py + 1);
+    acc += load_f(p + pz);
+    acc += load_f(p + pz + 1);
+    acc += load_f(p + pz + py);
+    acc += load_f(p + pz + py + 1);
+    return acc * 0.125f;
+}
+
+// Source values of columns (c, c+1) at row gy of plane z (MODE as above); the
+// second column repeats the first when c+1 is beyond the row (odd nx).
+template <int MODE, typename Tin>
+__device__ __forceinline__ float2 load_src_pair(const ConvXYArgs& a, const Tin* src, int z, int gy, int c, bool full) {
+    if constexpr (MODE == 0) {
+        using PT = typename Pair<Tin>::T;
+        return Pair<Tin>::get(*reinterpret_cast<const PT*>(src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py + c));
+    } else if constexpr (MODE == 1) {
+        const Tin* r = src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py;
+        const float v0 = load_f(r + c) * a.src_scale;
+        return make_float2(v0, full ? load_f(r + c + 1) * a.src_scale : v0);
+    } else {
+        const Tin* p = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy) * a.src_py + 2 * c;
+        const float v0 = sub_mean(p, a.src_py, a.src_pz);
+        return make_float2(v0, full ? sub_mean(p + 2, a.src_py, a.src_pz) : v0);
+    }
+}
+
+// x pass of one row pair over columns x0 .. x0+7 with radius RK from a line
+// whose apron is row_apron(RW); stores row 2rp to dst0 and row 2rp+1 to dst1
+// (null: beyond the volume).
+template <int RW, int RK>
+__device__ __forceinline__ void x_pass_rows(const float2* line, const Taps& taps, int x0, float* dst0, float* dst1) {
+    constexpr int AK = row_apron(RK);
+    constexpr int NE = (ROW_J + 2 * RK + (RK & 1) + 1) & ~1;   // window length (float2), even
+    float2 win[NE];                                          // win[i] is column x0 - AK + i
+    const float4* l4 = reinterpret_cast<const float4*>(line + x0 + row_apron(RW) - AK);
+#pragma unroll
+    for (int q = 0; q < NE / 2; ++q) {
+        const float4 t = l4[q];
+        win[2 * q] = make_float2(t.x, t.y);
+        win[2 * q + 1] = make_float2(t.z, t.w);
+    }
+    float2 o[ROW_J];
+#pragma unroll
+    for (int j = 0; j < ROW_J; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = -RK; k <= RK; ++k) acc = __ffma2_rn(f2(taps.w[k < 0 ? -k : k]), win[j + AK + k], acc);
+        o[j] = acc;
+    }
+    reinterpret_cast<float4*>(dst0)[0] = make_float4(o[0].x, o[1].x, o[2].x, o[3].x);
+    reinterpret_cast<float4*>(dst0)[1] = make_float4(o[4].x, o[5].x, o[6].x, o[7].x);
+    if (dst1 != nullptr) {
+        reinterpret_cast<float4*>(dst1)[0] = make_float4(o[0].y, o[1].y, o[2].y, o[3].y);
+        reinterpret_cast<float4*>(dst1)[1] = make_float4(o[4].y, o[5].y, o[6].y, o[7].y);
+    }
+}
+
+// RB > 0: also filter the same source rows with the descriptor pre-blur
+// (radius RB <= R, taps2) into dst2.
+template <int R, int MODE, typename Tin, typename Tbase, int RB>
+__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
+    static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
+    extern __shared__ __align__(16) float2 rows_sm[];
+    pdl_launch_dependents();
+    pdl_wait();
+    const int nx = a.nx;
+    const int W = row_line(nx, R);
+    constexpr int RA = row_apron(R);
+    float2* mid = rows_sm;                              // [ROW_TY/2][W]
+    float2* mid2 = rows_sm + (ROW_TY / 2) * W;          // same, pre-blur (RB > 0)
+    const int y0 = blockIdx.x * ROW_TY;
+    const int z = blockIdx.y;
+    const int tid = threadIdx.x;
+    const Tin* src = static_cast<const Tin*>(a.src);
+    if (a.zero_count != nullptr && y0 == 0 && z == 0 && tid < kDetectCounters) a.zero_count[tid] = 0;
+
+    // y pass
+    const int pairs = (nx + 1) / 2;
+    if (tid < 2 * pairs) {
+        const int p = tid % pairs, h = tid / pairs;
+        const int c = 2 * p, r0 = h * RY;
+        const bool full = c + 1 < nx;
+        float2 v[RY + 2 * R];
+#pragma unroll
+        for (int t = 0; t < RY + 2 * R; ++t)
+            v[t] = load_src_pair<MODE, Tin>(a, src, z, min(max(y0 + r0 - R + t, 0), a.ny - 1), c, full);
+        if constexpr (MODE == 2) {   // this CTA's own rows of the sub-sampled level are G_0
+            using PB = Pair<Tbase>;
+#pragma unroll
+            for (int j = 0; j < RY; ++j)
+                if (y0 + r0 + j < a.ny)
+                    reinterpret_cast<typename PB::T*>(static_cast<Tbase*>(a.base_out) + (int64_t)z * a.pz +
+                                                      (int64_t)(y0 + r0 + j) * a.py + c)[0] = PB::put(v[R + j]);
+        }
+#pragma unroll
+        for (int j = 0; j < RY; j += 2) {
+            float2 e = make_float2(0.f, 0.f), f = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = -R; k <= R; ++k) {
+                const float2 w = f2(a.taps.w[k < 0 ? -k : k]);
+                e = __ffma2_rn(w, v[j + R + k], e);
+                f = __ffma2_rn(w, v[j + 1 + R + k], f);
+            }
+            reinterpret_cast<float4*>(mid + ((r0 + j) / 2) * W + RA + c)[0] = make_float4(e.x, f.x, e.y, f.y);
+            if constexpr (RB > 0) {
+                e = make_float2(0.f, 0.f);
+                f = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = -RB; k <= RB; ++k) {
+                    const float2 w = f2(a.taps2.w[k < 0 ? -k : k]);
+                    e = __ffma2_rn(w, v[j + R + k], e);
+                    f = __ffma2_rn(w, v[j + 1 + R + k], f);
+                }
+                reinterpret_cast<float4*>(mid2 + ((r0 + j) / 2) * W + RA + c)[0] = make_float4(e.x, f.x, e.y, f.y);
+            }
+        }
+    }
+    __syncthreads();
+    // aprons: left copies of column 0, right copies of column nx-1 (this also
+    // overwrites the duplicate a pair wrote at column nx for odd nx)
+    {
+        const int right = W - (RA + nx);
+        const int per_line = RA + right;
+        const int nb = RB > 0 ? 2 : 1;
+        for (int i = tid; i < nb * (ROW_TY / 2) * per_line; i += blockDim.x) {
+            const int bsel = i / ((ROW_TY / 2) * per_line);
+            const int rem = i - bsel * (ROW_TY / 2) * per_line;
+            const int rp = rem / per_line, e = rem - rp * per_line;
+            float2* line = (bsel == 0 ? mid : mid2) + rp * W;
+            if (e < RA) line[e] = line[RA];
+            else line[RA + nx + (e - RA)] = line[RA + nx - 1];
+        }
+    }
+    __syncthreads();
+
+    // x pass
+    const int groups = (nx + ROW_J - 1) / ROW_J;
+    for (int item = tid; item < (ROW_TY / 2) * groups; item += blockDim.x) {
+        const int rp = item % (ROW_TY / 2);
+        const int g = item / (ROW_TY / 2);
+        const int x0 = g * ROW_J;
+        const int y = y0 + 2 * rp;
+        if (y >= a.ny) continue;
+        const int64_t off = (int64_t)z * a.pz + (int64_t)y * a.py + x0;
+        const bool second = y + 1 < a.ny;
+        x_pass_rows<R, R>(mid + rp * W, a.taps, x0, a.dst + off, second ? a.dst + off + a.py : nullptr);
+        if constexpr (RB > 0)
+            x_pass_rows<R, RB>(mid2 + rp * W, a.taps2, x0, a.dst2 + off, second ? a.dst2 + off + a.py : nullptr);
+    }
 }
 
 // ---- dispatch tables over the radius -------------------------------------
@@ -142,23 +332,20 @@ const void* xy_func_table(int r, int* smem, std::integer_sequence<int, Rs...>) {
     return fns[r - 1];
 }
 
-template <int TY, typename Tin, bool SUB, typename Tbase, int... Rs>
+template <int MODE, typename Tin, typename Tbase, int... Rs>
 const void* row_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, TY, Tin, SUB, Tbase, 0>)...};
-    const int sm[] = {row_smem_bytes<Rs + 1, TY>(nx)...};
-    *smem = sm[r - 1];
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, MODE, Tin, Tbase, 0>)...};
+    *smem = row_smem(nx, r, 0);
     return fns[r - 1];
 }
 
 // Fused pre-blur variants exist for radii >= kFusedBlurRadius (index r-RB).
-template <int TY, typename Tin, int... Rs>
+template <typename Tin, int... Rs>
 const void* row_blur_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
     constexpr int RB = kFusedBlurRadius;
-    const void* fns[] = {
-        reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + RB, TY, Tin, false, float, RB>)...};
-    const int sm[] = {(row_smem_bytes<Rs + RB, TY>(nx) + TY * row_pitch(nx) * 4)...};
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + RB, 0, Tin, float, RB>)...};
     if (r < RB) return nullptr;
-    *smem = sm[r - RB];
+    *smem = row_smem(nx, r, RB);
     return fns[r - RB];
 }
 
@@ -185,11 +372,9 @@ const void* xy_func(int r, int* smem) {
     return xy_func_table<Tin, SUB, Tbase>(r, smem, RadiusSeq{});
 }
 
-constexpr int ROW_TY = 16;
-
-template <typename Tin, bool SUB, typename Tbase>
+template <int MODE, typename Tin, typename Tbase>
 const void* row_func(int r, int nx, int* smem) {
-    return row_func_table<ROW_TY, Tin, SUB, Tbase>(r, nx, smem, RadiusSeq{});
+    return row_func_table<MODE, Tin, Tbase>(r, nx, smem, RadiusSeq{});
 }
 
 }  // namespace
@@ -200,32 +385,32 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const C
     if (radius < 1 || radius > kMaxRadius) return s;
     if (a.dst2 != nullptr) {   // level pass with the descriptor pre-blur fused in
         if (sub || src_kind != 2 || a.nx > ROW_MAX_NX) return s;
-        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<ROW_TY, float>(radius, a.nx, &smem, BlurRadiusSeq{});
-        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<ROW_TY, __half>(radius, a.nx, &smem, BlurRadiusSeq{});
-        else s.func = row_blur_func_table<ROW_TY, __nv_bfloat16>(radius, a.nx, &smem, BlurRadiusSeq{});
+        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<float>(radius, a.nx, &smem, BlurRadiusSeq{});
+        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<__half>(radius, a.nx, &smem, BlurRadiusSeq{});
+        else s.func = row_blur_func_table<__nv_bfloat16>(radius, a.nx, &smem, BlurRadiusSeq{});
         if (s.func == nullptr) return s;
         if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
-        s.block = dim3((a.nx + 31) / 32 * 32);
+        s.block = dim3(row_threads(a.nx));
         s.smem = smem;
         s.name = "conv_xy_blur";
         return s;
     }
     if (a.nx <= ROW_MAX_NX) {
         if (!sub) {
-            if (src_kind == 0) s.func = row_func<float, false, float>(radius, a.nx, &smem);
-            else if (src_kind == 1) s.func = row_func<uint8_t, false, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F32) s.func = row_func<float, false, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<__half, false, float>(radius, a.nx, &smem);
-            else s.func = row_func<__nv_bfloat16, false, float>(radius, a.nx, &smem);
+            if (src_kind == 0) s.func = row_func<1, float, float>(radius, a.nx, &smem);
+            else if (src_kind == 1) s.func = row_func<1, uint8_t, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F32) s.func = row_func<0, float, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<0, __half, float>(radius, a.nx, &smem);
+            else s.func = row_func<0, __nv_bfloat16, float>(radius, a.nx, &smem);
         } else {
-            if (storage == SIFT3D_STORAGE_F32) s.func = row_func<float, true, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<__half, true, __half>(radius, a.nx, &smem);
-            else s.func = row_func<__nv_bfloat16, true, __nv_bfloat16>(radius, a.nx, &smem);
+            if (storage == SIFT3D_STORAGE_F32) s.func = row_func<2, float, float>(radius, a.nx, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<2, __half, __half>(radius, a.nx, &smem);
+            else s.func = row_func<2, __nv_bfloat16, __nv_bfloat16>(radius, a.nx, &smem);
         }
         if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
-        s.block = dim3((a.nx + 31) / 32 * 32);
+        s.block = dim3(row_threads(a.nx));
         s.smem = smem;
         s.name = sub ? "conv_xy_sub" : "conv_xy";
         return s;
@@ -258,7 +443,7 @@ LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
     } else if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
     else if (storage == SIFT3D_STORAGE_F16) s.func = z_func_table<__half>(radius, RadiusSeq{});
     else s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
-    s.grid = dim3((unsigned)((a.pz + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
+    s.grid = dim3((unsigned)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
     s.block = dim3(Z_THREADS);
     s.smem = 0;
     s.name = a.dst2 ? "conv_z_dog_blur" : (a.dog ? "conv_z_dog" : "conv_z");

@@ -1,47 +1,356 @@
 // 4D extremum detection for sm_103a (Sec. 2.2.2 "4D Peak Detection").
 //
 // For every interior voxel v of an octave and every detection scale s = 1..S:
-//   1. contrast  |D_s(v)| >= t_c (cheap, and it rejects almost every voxel);
+//   1. contrast  |D_s(v)| >= t_c;
 //   2. sum of signs  S = sum over the 80 neighbours n (3x3x3 in D_{s-1} and
 //      D_{s+1}, 3x3x3 minus v in D_s) of sign(D_s(v) - D(n)); keep |S| >= cut
 //      (+-80 = strict peak / valley, the paper's default interval);
 //   3. curvature  H' = -sign(S) * Hessian(D_s at v) positive definite (leading
 //      minors) and tr(H')^3 r^2 < (2r+1)^3 det(H').
-// A CTA stages its 32x8x8 tile of D_1..D_S (plus a one-voxel halo) in shared
-// memory, so the neighbour reads are shared-memory reads; D_0 and D_{S+1} are
-// read from global memory only for voxels that survive the in-scale
-// comparisons.  A branch-free first pass applies exact necessary conditions to
-// every voxel-scale (contrast, the same voxel in D_{s-1} and D_{s+1}, the six
-// face neighbours); the ~1% that survive are listed in shared memory and get
-// the full test in a second pass spread over all lanes.  Keypoints are
-// compacted without an extrema map: a warp ballot, an intra-warp prefix (popc
-// of the lower lanes) and one atomicAdd per warp that has any.  A rank sort then writes
-// the records in canonical order (octave, scale, iz, iy, ix).  A single-CTA bitonic sort then writes the
-// records to the caller in the canonical order (octave, scale, iz, iy, ix).
+//
+// One CTA of 32x8 threads owns a 32x8x8 voxel tile.  A single 4D TMA load
+// (x, y, z, level) brings the tile plus a one-voxel halo of all S+2 DoG levels
+// into shared memory; the DoG levels of an octave lie at a constant stride in
+// the workspace, so the level is simply the fourth tensor dimension.  Halo
+// voxels outside the volume are zero-filled by the TMA unit; they are never
+// compared, because every detected voxel is at least `border` >= 1 voxels from
+// each face.
+//
+// Pass 1 (branch free): each thread walks its (x, y) column through the 8
+// planes with a register window over z and applies the exact necessary
+// conditions of a strict extremum: the contrast test and the eight nearest
+// comparisons (six faces in D_s, the same voxel in D_{s-1} and D_{s+1}).
+// Survivors are listed in shared memory.  Pass 2 runs the full 80-neighbour sum
+// (faces, edges and corners of D_s, then D_{s-1}, then D_{s+1}; it stops once
+// the cut is out of reach) and the curvature test, spread over all lanes.
+// Keypoints are compacted without an extrema map: a warp ballot, an intra-warp
+// prefix (popc of the lower lanes) and one atomicAdd per warp.  A rank sort
+// then writes the records to the caller in canonical order (octave, scale, iz,
+// iy, ix), independent of scheduling.
 #include <algorithm>
 
-#include "peak_tile.cuh"
+#include "common.cuh"
 
 namespace sift3d {
 
 namespace {
 
-using namespace peak_detail;
+constexpr int TX = 32, TY = 8, TZ = 8;
+constexpr int THREADS = TX * TY;
+constexpr int SY = TY + 2, SZ = TZ + 2;
+constexpr int SURV = 512;                     // pass-2 list of one CTA
+
+// Staged row width: the 34 voxels of a halo row rounded up so that the TMA box
+// row is a multiple of 16 bytes.
+template <typename S>
+__host__ __device__ constexpr int box_w() { return sizeof(S) == 4 ? 36 : 40; }
 
 template <typename S>
-__global__ void __launch_bounds__(PK_THREADS, 3) peak_kernel(const PeakArgs a) {
-    extern __shared__ float pk_sm[];
-    __shared__ unsigned surv[PK_SURV];
+__host__ __device__ constexpr int level_elems() { return box_w<S>() * SY * SZ; }
+
+template <typename S>
+constexpr size_t peak_smem(int n_levels) { return (size_t)n_levels * level_elems<S>() * sizeof(S); }
+
+// The 80 neighbours as (dx, dy, dz, level offset): the 26 of D_s first (faces,
+// then edges, then corners: the likeliest to break an extremum early), then the
+// 27 of D_{s-1} and the 27 of D_{s+1}.
+struct NbrTable {
+    int v[80][4];
+};
+
+__host__ __device__ constexpr NbrTable make_nbr_table() {
+    NbrTable t{};
+    int n = 0;
+    for (int order = 1; order <= 3; ++order)          // number of non-zero offsets
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int m = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (m == order) {
+                        t.v[n][0] = dx, t.v[n][1] = dy, t.v[n][2] = dz, t.v[n][3] = 0;
+                        ++n;
+                    }
+                }
+    for (int dl = -1; dl <= 1; dl += 2)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    t.v[n][0] = dx, t.v[n][1] = dy, t.v[n][2] = dz, t.v[n][3] = dl;
+                    ++n;
+                }
+    return t;
+}
+
+constexpr NbrTable kNbr = make_nbr_table();
+static_assert(kNbr.v[5][3] == 0 && kNbr.v[6][0] * kNbr.v[6][0] + kNbr.v[6][1] * kNbr.v[6][1] +
+                                           kNbr.v[6][2] * kNbr.v[6][2] == 2,
+              "faces first, then edges");
+static_assert(kNbr.v[25][3] == 0 && kNbr.v[26][3] == -1 && kNbr.v[79][3] == 1, "neighbour table layout");
+
+// Offsets of the 80 neighbours inside the staged levels (elements).
+struct OffTable {
+    int o[80];
+};
+
+template <typename S>
+__host__ __device__ constexpr OffTable make_off_table() {
+    const NbrTable t = make_nbr_table();
+    OffTable r{};
+    for (int k = 0; k < 80; ++k)
+        r.o[k] = ((t.v[k][3] * SZ + t.v[k][2]) * SY + t.v[k][1]) * box_w<S>() + t.v[k][0];
+    return r;
+}
+
+template <typename S>
+__device__ __forceinline__ float ld(const S* p) { return to_f32(*p); }
+
+// Neighbours K0..K1-1 around the staged centre p: all reads before any comparison.
+template <typename S, int K0, int K1>
+__device__ __forceinline__ void sign_batch(const S* p, float c, int& sum) {
+    constexpr OffTable T = make_off_table<S>();
+    float n[K1 - K0];
+#pragma unroll
+    for (int i = 0; i < K1 - K0; ++i) n[i] = ld(p + T.o[K0 + i]);
+#pragma unroll
+    for (int i = 0; i < K1 - K0; ++i) sum += (c > n[i]) - (c < n[i]);
+}
+
+template <int K1>
+__device__ __forceinline__ bool out_of_reach(int sum, int cut) {
+    return (sum < 0 ? -sum : sum) + (80 - K1) < cut;
+}
+
+// Sum-of-signs and curvature tests of the staged centre p (contrast already
+// passed); stores the sum of signs in *ssum.
+template <typename S>
+__device__ __forceinline__ bool full_test(const S* p, float c, int cut, float k1, float k2, int* ssum) {
+    // After k comparisons |S| can still change by at most 80 - k: stop once the
+    // cut is out of reach.
+    int sum = 0;
+    sign_batch<S, 0, 6>(p, c, sum);
+    if (out_of_reach<6>(sum, cut)) return false;
+    sign_batch<S, 6, 18>(p, c, sum);
+    if (out_of_reach<18>(sum, cut)) return false;
+    sign_batch<S, 18, 26>(p, c, sum);
+    if (out_of_reach<26>(sum, cut)) return false;
+    sign_batch<S, 26, 53>(p, c, sum);
+    if (out_of_reach<53>(sum, cut)) return false;
+    sign_batch<S, 53, 80>(p, c, sum);
+    if (out_of_reach<80>(sum, cut)) return false;
+    // curvature: H' = -sign(S) * Hessian of D_s by central differences
+    constexpr int BX = box_w<S>();
+    auto v = [&](int dz, int dy, int dx) { return ld(p + (dz * SY + dy) * BX + dx); };
+    const float hxx = v(0, 0, 1) + v(0, 0, -1) - 2.0f * c;
+    const float hyy = v(0, 1, 0) + v(0, -1, 0) - 2.0f * c;
+    const float hzz = v(1, 0, 0) + v(-1, 0, 0) - 2.0f * c;
+    const float hxy = (v(0, 1, 1) - v(0, -1, 1) - v(0, 1, -1) + v(0, -1, -1)) * 0.25f;
+    const float hxz = (v(1, 0, 1) - v(-1, 0, 1) - v(1, 0, -1) + v(-1, 0, -1)) * 0.25f;
+    const float hyz = (v(1, 1, 0) - v(-1, 1, 0) - v(1, -1, 0) + v(-1, -1, 0)) * 0.25f;
+    const float sg = sum > 0 ? -1.0f : 1.0f;
+    const float A = sg * hxx, B = sg * hyy, C = sg * hzz;
+    const float XY = sg * hxy, XZ = sg * hxz, YZ = sg * hyz;
+    const float m2 = A * B - XY * XY;
+    const float det = A * (B * C - YZ * YZ) - XY * (XY * C - YZ * XZ) + XZ * (XY * YZ - B * XZ);
+    const float tr = A + B + C;
+    const float g = k1 * det - k2 * (tr * tr * tr);
+    *ssum = sum;
+    return A > 0.f && m2 > 0.f && det > 0.f && g > 0.f;
+}
+
+__device__ __forceinline__ void write_keypoint(const PeakArgs& a, int slot, int x, int y, int z, int s, int ssum,
+                                               float c, float scale) {
+    sift3d_keypoint k;
+    k.x = ((float)x + 0.5f) * scale - 0.5f;
+    k.y = ((float)y + 0.5f) * scale - 0.5f;
+    k.z = ((float)z + 0.5f) * scale - 0.5f;
+    k.sigma = a.sigma_level[s] * scale;
+    k.ix = x;
+    k.iy = y;
+    k.iz = z;
+    k.octave = (int16_t)a.octave;
+    k.scale = (int16_t)s;
+    k.polarity = ssum > 0 ? 1 : -1;
+    k.reserved0[0] = k.reserved0[1] = k.reserved0[2] = 0;
+    k.dog = c;
+    k.sign_sum = ssum;
+    k.reserved1 = 0;
+    a.out[slot] = k;
+}
+
+// ---- mbarrier / TMA helpers (inline PTX) ------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int l,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(l),
+          "r"(smem_addr(bar))
+        : "memory");
+}
+
+constexpr int kWaitPolls = 1 << 20;
+
+template <typename S, int NS>
+__global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant__ PeakTmaArgs A) {
+    constexpr int NL = NS + 2;
+    constexpr int BX = box_w<S>();
+    constexpr int PL = SY * BX;            // one staged z plane
+    constexpr int LV = SZ * PL;            // one staged level
+    extern __shared__ __align__(128) unsigned char pk_raw[];
+    S* sm = reinterpret_cast<S*>(pk_raw);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned surv[SURV];
     __shared__ int n_surv;
-    pdl_launch_dependents();
-    pdl_wait();
-    peak_tile<S>(a, blockIdx.x, blockIdx.y, blockIdx.z, pk_sm, surv, n_surv);
+    const PeakArgs& a = A.a;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int tid = lane + TX * w;
+    const int xs = A.x_start + blockIdx.x * TX;           // halo origin of this tile
+    const int ys = a.border - 1 + blockIdx.y * TY;
+    const int zs = a.border - 1 + blockIdx.z * TZ;
+
+    if (tid == 0) {
+        n_surv = 0;
+        mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar, (unsigned)(NL * LV * sizeof(S)));
+        tma_load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar);
+    }
+    const bool staged = __syncthreads_and(mbar_wait_bounded(&bar, 0, kWaitPolls));
+    if (!staged) {
+        // The copy did not land in time: flag the detect as failed, give the
+        // copy a second bounded wait so no write is still in flight, and leave.
+        if (tid == 0) {
+            atomicExch(A.err, 1);
+            mbar_wait_bounded(&bar, 0, kWaitPolls);
+        }
+        __syncthreads();
+        return;
+    }
+
+    const int b = a.border;
+    const int x = xs + 1 + lane, y = ys + 1 + w;
+    const bool col_inside = x >= b && x < a.nx - b && y < a.ny - b;
+    const bool strict = a.sign_sum_min >= 80;
+    const float scale = (float)(1 << a.octave);
+    const S* col = sm + (w + 1) * BX + lane + 1;           // level 0, staged plane 0
+
+    // Pass 1 with a register window over z: D_l at planes z-1, z, z+1.
+    float prv[NL], cur[NL], nxt[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        prv[l] = ld(col + l * LV);
+        cur[l] = ld(col + l * LV + PL);
+    }
+#pragma unroll
+    for (int tz = 0; tz < TZ; ++tz) {
+        const int zz = tz + 1;
+        const bool inside = col_inside && zs + zz < a.nz - b;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) nxt[l] = ld(col + l * LV + (zz + 1) * PL);
+#pragma unroll
+        for (int s = 1; s <= NS; ++s) {
+            const S* p = col + s * LV + zz * PL;
+            const float c = cur[s];
+            const float f0 = ld(p - 1), f1 = ld(p + 1), f2 = ld(p - BX), f3 = ld(p + BX);
+            const float lo = cur[s - 1], hi = cur[s + 1], f4 = prv[s], f5 = nxt[s];
+            bool cand;
+            if (strict) {
+                const float mx = fmaxf(fmaxf(fmaxf(lo, hi), fmaxf(f0, f1)), fmaxf(fmaxf(f2, f3), fmaxf(f4, f5)));
+                const float mn = fminf(fminf(fminf(lo, hi), fminf(f0, f1)), fminf(fminf(f2, f3), fminf(f4, f5)));
+                cand = c > mx || c < mn;
+            } else {
+                const int s8 = (c > lo) - (c < lo) + (c > hi) - (c < hi) + (c > f0) - (c < f0) + (c > f1) - (c < f1) +
+                               (c > f2) - (c < f2) + (c > f3) - (c < f3) + (c > f4) - (c < f4) + (c > f5) - (c < f5);
+                cand = (s8 < 0 ? -s8 : s8) + 72 >= a.sign_sum_min;
+            }
+            if (inside && cand && fabsf(c) >= a.contrast) {
+                const int pos = atomicAdd(&n_surv, 1);
+                if (pos < SURV) {
+                    surv[pos] = (unsigned)lane | ((unsigned)w << 5) | ((unsigned)tz << 8) | ((unsigned)s << 12);
+                } else {
+                    // list full: test here (rare; same result, slower path)
+                    int ssum = 0;
+                    if (full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum)) {
+                        const int slot = atomicAdd(a.count, 1);
+                        if (slot < a.capacity) write_keypoint(a, slot, x, y, zs + zz, s, ssum, c, scale);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            prv[l] = cur[l];
+            cur[l] = nxt[l];
+        }
+    }
+    __syncthreads();
+
+    // Pass 2: the full 80-neighbour and curvature tests of the listed
+    // voxel-scales, 32 per warp at a time.
+    const int n = min(n_surv, SURV);
+    for (int base = w * 32; base < n; base += THREADS) {
+        const int i = base + lane;
+        bool kp = false;
+        int ssum = 0, kx = 0, ky = 0, kz = 0, s = 1;
+        float c = 0.f;
+        if (i < n) {
+            const unsigned e = surv[i];
+            const int l = e & 31, ww = (e >> 5) & 7, tz = (e >> 8) & 7;
+            s = (e >> 12) & 7;
+            kx = xs + 1 + l, ky = ys + 1 + ww, kz = zs + 1 + tz;
+            const S* p = sm + s * LV + (tz + 1) * PL + (ww + 1) * BX + l + 1;
+            c = ld(p);
+            kp = full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, kp);
+        if (m == 0u) continue;
+        const int leader = __ffs(m) - 1;
+        int slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(a.count, __popc(m));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (!kp) continue;
+        const int slot = slot0 + __popc(m & ((1u << lane) - 1u));
+        if (slot < a.capacity) write_keypoint(a, slot, kx, ky, kz, s, ssum, c, scale);
+    }
 }
 
 // ---- canonical order ------------------------------------------------------
 // Rank sort: the key of record i packs (octave, scale, iz, iy, ix, i), so keys
 // are unique and record i's place is the number of smaller keys.  Each CTA
-// ranks 1024 records against all keys, read through shared memory in tiles.
+// ranks 128 records against all keys, read through shared memory in tiles.
 constexpr int SORT_THREADS = 128;
 constexpr int SORT_TILE = kSortSmemKeys;
 
@@ -71,17 +380,63 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
     if (i < n) a.out[rank] = a.staging[i];
 }
 
+template <typename S>
+const void* peak_func(int ns) {
+    switch (ns) {
+        case 1: return reinterpret_cast<const void*>(&peak_kernel<S, 1>);
+        case 2: return reinterpret_cast<const void*>(&peak_kernel<S, 2>);
+        case 3: return reinterpret_cast<const void*>(&peak_kernel<S, 3>);
+        case 4: return reinterpret_cast<const void*>(&peak_kernel<S, 4>);
+        case 5: return reinterpret_cast<const void*>(&peak_kernel<S, 5>);
+        default: return nullptr;
+    }
+}
+
+template <typename S>
+void peak_geometry(const PeakArgs& a, int* x_start, int* box_x, int* gx, size_t* smem) {
+    // The first halo origin is border-1 rounded down to 8 voxels, so that every
+    // tile's TMA x coordinate is 16-byte aligned for 4- and 2-byte elements.
+    *x_start = ((a.border - 1) / 8) * 8;
+    *box_x = box_w<S>();
+    const int covered = a.nx - a.border - (*x_start + 1);    // x = x_start+1 .. nx-border-1
+    *gx = std::max(1, (covered + TX - 1) / TX);
+    *smem = peak_smem<S>(a.n_scales + 2);
+}
+
 }  // namespace
 
-LaunchSpec peak_spec(int storage, const PeakArgs& a) {
+void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z) {
+    int gx;
+    size_t smem;
+    if (storage == SIFT3D_STORAGE_F32) peak_geometry<float>(a, x_start, box_x, &gx, &smem);
+    else peak_geometry<__half>(a, x_start, box_x, &gx, &smem);
+    *box_y = SY;
+    *box_z = SZ;
+}
+
+LaunchSpec peak_spec(int storage, const PeakTmaArgs& A) {
     LaunchSpec s;
-    if (storage == SIFT3D_STORAGE_F32) s.func = reinterpret_cast<const void*>(&peak_kernel<float>);
-    else if (storage == SIFT3D_STORAGE_F16) s.func = reinterpret_cast<const void*>(&peak_kernel<__half>);
-    else s.func = reinterpret_cast<const void*>(&peak_kernel<__nv_bfloat16>);
-    const int ix = a.nx - 2 * a.border, iy = a.ny - 2 * a.border, iz = a.nz - 2 * a.border;
-    s.grid = dim3((ix + PK_BX - 1) / PK_BX, (iy + PK_BY - 1) / PK_BY, (iz + PK_TZ - 1) / PK_TZ);
-    s.block = dim3(PK_BX, PK_BY);
-    s.smem = peak_smem_bytes(a.n_scales);
+    const PeakArgs& a = A.a;
+    int x_start = 0, box_x = 0, gx = 1;
+    size_t smem = 0;
+    if (storage == SIFT3D_STORAGE_F32) {
+        s.func = peak_func<float>(a.n_scales);
+        peak_geometry<float>(a, &x_start, &box_x, &gx, &smem);
+    } else if (storage == SIFT3D_STORAGE_F16) {
+        s.func = peak_func<__half>(a.n_scales);
+        peak_geometry<__half>(a, &x_start, &box_x, &gx, &smem);
+    } else {
+        s.func = peak_func<__nv_bfloat16>(a.n_scales);
+        peak_geometry<__nv_bfloat16>(a, &x_start, &box_x, &gx, &smem);
+    }
+    if (s.func == nullptr || x_start != A.x_start) {
+        s.func = nullptr;
+        return s;
+    }
+    const int iy = a.ny - 2 * a.border, iz = a.nz - 2 * a.border;
+    s.grid = dim3(gx, (iy + TY - 1) / TY, (iz + TZ - 1) / TZ);
+    s.block = dim3(TX, TY);
+    s.smem = smem;
     if (s.smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     s.name = "peak";
     return s;

@@ -3,6 +3,8 @@
 // the detect DAG and its execution.
 #include "runtime.hpp"
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -408,6 +410,50 @@ PeakArgs make_peak_args(const Workspace& ws, int o) {
     return pa;
 }
 
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    // The driver entry point, looked up once (no link-time dependency on libcuda).
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        (void)cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+}  // namespace
+
+bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
+    const Plan& pl = ws.plan;
+    const OctaveGeom& g = pl.oct[o];
+    PeakTmaArgs& A = *out;
+    memset(&A, 0, sizeof(A));
+    A.a = make_peak_args(ws, o);
+    A.err = ws.count + 3;
+    int box_x, box_y, box_z;
+    peak_layout(pl.p.storage, A.a, &A.x_start, &box_x, &box_y, &box_z);
+    const size_t stride = pl.off_D[o][1] - pl.off_D[o][0];
+    for (int s = 1; s + 1 < pl.nD; ++s)
+        if (pl.off_D[o][s + 1] - pl.off_D[o][s] != stride) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc == nullptr) return false;
+    const CUtensorMapDataType dt = pl.p.storage == SIFT3D_STORAGE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : pl.p.storage == SIFT3D_STORAGE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)pl.nD};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.py * pl.elem, (cuuint64_t)g.pz * pl.elem, (cuuint64_t)stride};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)pl.nD};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(&A.dogs, dt, 4, ws.D(o, 0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ---- detect DAG ---------------------------------------------------------------
 std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* first_node, int* sort_node) {
     const Plan& pl = ws.plan;
@@ -524,8 +570,11 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         if (o > 0) g_node[o][0] = g_node[o][1];
         // peak detection on D_1..D_S
         if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
-            const PeakArgs pa = make_peak_args(ws, o);
-            peak_nodes.push_back(add(peak_spec(st, pa), pa, {g_node[o][pl.L - 1]}));
+            PeakTmaArgs pa;
+            LaunchSpec ps;
+            if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
+            else ps.name = "peak (DoG tensor map)";
+            peak_nodes.push_back(add(ps, pa, {g_node[o][pl.L - 1]}));
             // D_1..D_S must be read in full; D_0 and D_{S+1} only around candidates
             tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
         }
@@ -698,7 +747,7 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         ex.nodes = build_detect(ws, c, &ex.first, &ex.sort);
         for (auto& n : ex.nodes)
             if (n.spec.func == nullptr) {
-                if (err) *err = "no kernel instance for this configuration";
+                if (err) *err = std::string("no kernel instance for this configuration: ") + n.spec.name;
                 ex.nodes.clear();
                 return SIFT3D_EINVAL;
             }

@@ -79,6 +79,8 @@ int alloc_device_zeroed(size_t bytes, char** out, std::string* err);
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
 void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin);
 PeakArgs make_peak_args(const Workspace& ws, int o);
+// Peak kernel arguments with the octave's DoG tensor map; false if it cannot be encoded.
+bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out);
 void free_workspace(Workspace* ws);
 
 // One kernel launch of the detect DAG with its argument bytes and dependencies.
