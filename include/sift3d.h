@@ -116,11 +116,15 @@ typedef struct sift3d_params {
     uint64_t hbm_budget_bytes;   /* serving admission budget (0 = 40 GiB)      */
     int32_t  max_keypoints;      /* serving: keypoints kept per request (8192) */
     int32_t  max_inflight;       /* serving: requests on the device at once (4) */
-    int32_t  fuse_small_octaves; /* 0 = one launch per pass (default); 1 =
-                                    octaves after the first (<= 4M voxels) run
-                                    in one cooperative launch                  */
+    int32_t  fuse_small_octaves; /* 0 (default) = one launch per pass; 1 =
+                                    the last octaves of at most 32768 voxels
+                                    whose z-slabs fit the shared memory of a
+                                    thread-block cluster build their pyramids
+                                    in one cluster launch (bitwise the same
+                                    results; measured slower on GB300)       */
     int32_t  use_pdl;            /* 0 (default); 1 = chain the detect graph's
-                                    kernels with programmatic dependent launch */
+                                    kernels with programmatic dependent launch;
+                                    2 = only between kernels of octaves >= 1 */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

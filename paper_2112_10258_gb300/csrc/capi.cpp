@@ -112,7 +112,7 @@ int get_entry(sift3d_ctx* c, int nx, int ny, int nz, int dtype, int capacity, De
 
 int launch(const LaunchSpec& s, void* argp, cudaStream_t st, std::string* err) {
     void* args[1] = {argp};
-    cudaError_t e = cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
+    cudaError_t e = launch_spec(s, args, st);
     if (e != cudaSuccess) {
         if (err) *err = std::string(s.name) + ": " + cudaGetErrorString(e);
         return SIFT3D_ECUDA;

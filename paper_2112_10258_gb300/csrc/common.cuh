@@ -150,24 +150,31 @@ struct ReadLevelArgs {
     float* dst;
 };
 
-// ---- octave-tail kernel: phases of tile tasks in one cooperative launch -------
-struct TailTask {
-    enum Type : int { XY = 0, XY_SUB = 1, Z = 2, PEAK = 3 };
-    int type;
-    int radius;
-    int n_tiles;
-    int reserved;
-    ConvXYArgs xy;
-    ConvZArgs z;
-    PeakArgs pk;
+// ---- small-octave kernel: the pyramids of the last octaves in one cluster ----
+constexpr int kTailCluster = 16;     // CTAs of the cluster where the device can hold it
+constexpr int kTailClusterPortable = 8;   // otherwise
+constexpr int kTailMaxSlab = 5;      // z planes per CTA (octave nz <= cluster * 5)
+
+struct TailOctave {
+    int nx, ny, nz;
+    int64_t py, pz;                         // level pitches (elements)
+    void* G[kMaxLevels];                    // G_0..G_{S+2} (storage type)
+    void* D[kMaxDogs];                      // D_0..D_{S+1}
+    void* B[SIFT3D_MAX_SCALES];             // pre-blurred G_1..G_S (when r_desc > 0)
 };
 
 struct TailArgs {
-    const TailTask* tasks;
-    const int* phase_begin;     // n_phases + 1 entries into tasks
-    int n_phases;
-    int* bar;                   // monotone barrier counter (zeroed per detect)
-    int* err;                   // set when a barrier wait runs out
+    int n_oct;                              // octaves run by the kernel
+    int max_nz;                             // largest nz among them
+    int slab_planes;                        // planes per shared slab buffer: ceil(max_nz / cluster)
+    int L, S;                               // Gaussian levels and scales per octave
+    const void* src;                        // level S of the octave before the first one
+    int64_t src_py, src_pz;
+    int r_inc[kMaxLevels];                  // radius and taps of level s = index + 1
+    Taps t_inc[kMaxLevels];
+    int r_desc;                             // descriptor pre-blur (0 = none)
+    Taps t_desc;
+    TailOctave oct[SIFT3D_MAX_OCTAVES];
 };
 
 // A kernel launch with its single by-value argument struct, usable both for a
@@ -177,7 +184,11 @@ struct LaunchSpec {
     dim3 grid, block;
     size_t smem = 0;
     const char* name = "";
+    int cluster = 0;          // > 0: thread-block cluster of this many CTAs along x
 };
+
+// Launch of a spec on a stream (cluster launches go through cudaLaunchKernelEx).
+cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st);
 
 // Launch builders (one per kernel family).  `storage` is SIFT3D_STORAGE_*,
 // `src_kind` for conv_xy is 0 = float32, 1 = uint8, 2 = storage type.
@@ -187,8 +198,10 @@ LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
-LaunchSpec tail_spec(int storage, int n_scales, int max_ctas);
-int tail_tiles(const TailTask& t);
-int tail_smem_bytes(int n_scales);
+LaunchSpec tail_spec(int storage, const TailArgs& a);
+int tail_cluster_size(int storage, const TailArgs& a);   // 16, 8, or 0 (cannot run)
+// Row pitch of the small-octave kernel's shared slabs (odd: conflict-free columns).
+__host__ __device__ constexpr int tail_row_pitch(int nx) { return nx | 1; }
+size_t tail_smem_bytes(int plane_elems, int slab_planes);   // dynamic shared memory of the small-octave kernel
 
 }  // namespace sift3d

@@ -1,5 +1,5 @@
-// Device bodies of the separable-convolution tiles (see conv.cu), shared by
-// the conv kernels and the octave-tail kernel.
+// Tile body of the y/x pass for rows wider than 256 (see conv.cu) and the
+// constants the conv kernels share.
 #pragma once
 
 #include "common.cuh"
@@ -11,7 +11,7 @@ constexpr int XY_TX = 64;
 constexpr int XY_TY = 32;
 constexpr int XY_J = 8;          // outputs per thread in each pass
 constexpr int XY_THREADS = 256;
-constexpr int Z_TZ = 16;
+constexpr int Z_TZ = 16;          // conv_z outputs per thread
 constexpr int Z_THREADS = 128;
 
 template <int R>
@@ -133,101 +133,9 @@ __device__ __forceinline__ void conv_xy_tile(const ConvXYArgs& a, int bx, int by
 }
 
 
-// ---- full-row variant (nx <= 256): one thread per column, no x halo ----------
-// The CTA stages rows y0-R .. y0+TY+R-1 (clamped) of one plane at full width;
-// thread c filters column c along y from a register window (TY outputs), then
-// each thread filters groups of 8 outputs along x reading shared memory with the
-// column index clamped to [0, nx-1], which is the clamp-to-edge border.  No
-// halo column is filtered and no thread covers a column beyond the row.
+// Rows up to this width take the full-row kernel (conv.cu); wider ones the tiles above.
 constexpr int ROW_MAX_NX = 256;
-constexpr int ROW_J = 8;
-
-__host__ __device__ constexpr int row_pitch(int nx) { return ((nx + 7) & ~7) | 1; }
-
-template <int R, int TY>
-__host__ __device__ constexpr int row_smem_bytes(int nx) {
-    return (TY + 2 * R + TY) * row_pitch(nx) * 4;
-}
-
-template <typename Tin, bool SUB>
-__device__ __forceinline__ float stage_value(const ConvXYArgs& a, const Tin* src, int z, int gy, int gx) {
-    if constexpr (!SUB) {
-        return load_f(src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py + gx) * a.src_scale;
-    } else {
-        const Tin* p = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy) * a.src_py + 2 * gx;
-        float acc = 0.f;
-        acc += load_f(p);
-        acc += load_f(p + 1);
-        acc += load_f(p + a.src_py);
-        acc += load_f(p + a.src_py + 1);
-        acc += load_f(p + a.src_pz);
-        acc += load_f(p + a.src_pz + 1);
-        acc += load_f(p + a.src_pz + a.src_py);
-        acc += load_f(p + a.src_pz + a.src_py + 1);
-        return acc * 0.125f;
-    }
-}
-
-
-// Column col, planes z0 .. z0+TZ-1.
-template <int R, typename S, bool COHERENT, int RB>
-__device__ __forceinline__ void conv_z_column(const ConvZArgs& a, int64_t col, int z0) {
-    // Columns are addressed linearly inside a plane (pitch layout, padding
-    // columns included): the z pass does not care about x/y structure.  Each
-    // thread holds TZ + 2R inputs of one column and, for the DoG, the TZ values
-    // of G_{s-1}; every load is issued before the first store, so a thread waits
-    // for memory once (the stores could alias the loads as far as the compiler
-    // knows, which would otherwise serialise each output behind its own load).
-    // COHERENT: plain loads (the octave-tail kernel rewrites its inputs between
-    // phases, so the read-only path may not be used there).
-    if (col >= a.pz) return;
-    const bool with_dog = a.dog != nullptr;
-    float v[Z_TZ + 2 * R];
-#pragma unroll
-    for (int t = 0; t < Z_TZ + 2 * R; ++t) {
-        const int zz = min(max(z0 - R + t, 0), a.nz - 1);
-        const float* p = a.src + (int64_t)zz * a.pz + col;
-        v[t] = COHERENT ? *p : __ldg(p);
-    }
-    float u[RB > 0 ? Z_TZ + 2 * RB : 1];   // second intermediate (fused pre-blur)
-    if constexpr (RB > 0) {
-#pragma unroll
-        for (int t = 0; t < Z_TZ + 2 * RB; ++t) {
-            const int zz = min(max(z0 - RB + t, 0), a.nz - 1);
-            const float* p = a.src2 + (int64_t)zz * a.pz + col;
-            u[t] = COHERENT ? *p : __ldg(p);
-        }
-    }
-    float pv[Z_TZ];
-    if (with_dog) {
-        const S* prev = static_cast<const S*>(a.prev);
-#pragma unroll
-        for (int j = 0; j < Z_TZ; ++j) {
-            const int zz = min(z0 + j, a.nz - 1);
-            pv[j] = to_f32(prev[(int64_t)zz * a.pz + col]);
-        }
-    }
-    S* dst = static_cast<S*>(a.dst);
-    S* dog = static_cast<S*>(a.dog);
-#pragma unroll
-    for (int j = 0; j < Z_TZ; ++j) {
-        const int z = z0 + j;
-        if (z >= a.nz) break;
-        float acc = 0.f;
-#pragma unroll
-        for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], v[j + R + k], acc);
-        const int64_t off = (int64_t)z * a.pz + col;
-        dst[off] = from_f32<S>(acc);
-        if (with_dog) dog[off] = from_f32<S>(pv[j] - acc);
-        if constexpr (RB > 0) {
-            float acc2 = 0.f;
-#pragma unroll
-            for (int k = -RB; k <= RB; ++k) acc2 = fmaf(a.taps2.w[k < 0 ? -k : k], u[j + RB + k], acc2);
-            static_cast<S*>(a.dst2)[off] = from_f32<S>(acc2);
-        }
-    }
-}
-
+constexpr int ROW_J = 8;          // outputs per thread of the full-row x pass
 
 }  // namespace conv_detail
 }  // namespace sift3d

@@ -30,6 +30,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace sift3d {
 
@@ -177,48 +178,17 @@ __device__ __forceinline__ void write_keypoint(const PeakArgs& a, int slot, int 
     a.out[slot] = k;
 }
 
-// ---- mbarrier / TMA helpers (inline PTX) ------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
+// Full test of a voxel-scale that found the pass-2 list full (rare): kept out
+// of line so that the unrolled pass-1 loop holds one call, not 24 copies.
+template <typename S>
+__device__ __noinline__ void test_overflow(const PeakArgs& a, const S* p, float c, int x, int y, int z, int s,
+                                           float scale) {
+    int ssum = 0;
+    if (full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum)) {
+        const int slot = atomicAdd(a.count, 1);
+        if (slot < a.capacity) write_keypoint(a, slot, x, y, z, s, ssum, c, scale);
+    }
 }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of the barrier at most `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
-    for (int i = 0; i < limit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int l,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(l),
-          "r"(smem_addr(bar))
-        : "memory");
-}
-
-constexpr int kWaitPolls = 1 << 20;
 
 template <typename S, int NS>
 __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant__ PeakTmaArgs A) {
@@ -238,27 +208,12 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
     const int ys = a.border - 1 + blockIdx.y * TY;
     const int zs = a.border - 1 + blockIdx.z * TZ;
 
-    if (tid == 0) {
-        n_surv = 0;
-        mbar_init(&bar, 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(&bar, (unsigned)(NL * LV * sizeof(S)));
-        tma_load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar);
-    }
-    const bool staged = __syncthreads_and(mbar_wait_bounded(&bar, 0, kWaitPolls));
-    if (!staged) {
-        // The copy did not land in time: flag the detect as failed, give the
-        // copy a second bounded wait so no write is still in flight, and leave.
-        if (tid == 0) {
-            atomicExch(A.err, 1);
-            mbar_wait_bounded(&bar, 0, kWaitPolls);
-        }
-        __syncthreads();
-        return;
-    }
+    pdl_launch_dependents();
+    pdl_wait();     // the DoG levels are complete (no-op without a programmatic edge)
+    if (tid == 0) n_surv = 0;
+    const bool staged = tma::stage_tile(&bar, (unsigned)(NL * LV * sizeof(S)), A.err,
+                                        [&] { tma::load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar); });
+    if (!staged) return;   // error flag set; the whole CTA leaves together
 
     const int b = a.border;
     const int x = xs + 1 + lane, y = ys + 1 + w;
@@ -301,12 +256,7 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
                 if (pos < SURV) {
                     surv[pos] = (unsigned)lane | ((unsigned)w << 5) | ((unsigned)tz << 8) | ((unsigned)s << 12);
                 } else {
-                    // list full: test here (rare; same result, slower path)
-                    int ssum = 0;
-                    if (full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum)) {
-                        const int slot = atomicAdd(a.count, 1);
-                        if (slot < a.capacity) write_keypoint(a, slot, x, y, zs + zz, s, ssum, c, scale);
-                    }
+                    test_overflow<S>(a, p, c, x, y, zs + zz, s, scale);   // list full: same result, slower
                 }
             }
         }

@@ -65,6 +65,9 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.storage < SIFT3D_STORAGE_F32 || p.storage > SIFT3D_STORAGE_BF16) return fail(err, "bad storage");
     if (p.max_keypoints < 0 || p.max_keypoints > (1 << 20)) return fail(err, "max_keypoints must be in 0..2^20");
     if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
+    if (p.use_pdl < 0 || p.use_pdl > 2) return fail(err, "use_pdl must be 0, 1 or 2");
+    if (p.fuse_small_octaves < 0 || p.fuse_small_octaves > 1) return fail(err, "fuse_small_octaves must be 0 or 1");
+
     // filter radii of the schedule
     const int S = p.scales_per_octave;
     double sig[kMaxLevels];
@@ -122,13 +125,19 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
         cz /= 2;
     }
     if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
+    // The small-octave kernel takes the longest run of last octaves (from
+    // octave 1 on) of at most kTailMaxVoxels voxels whose z-slabs fit its
+    // shared memory: ceil(nz / 8) planes of each level per CTA.
     pl.tail_start = pl.nO;
     if (p.fuse_small_octaves)
-        for (int o = 1; o < pl.nO; ++o)
-            if (pl.oct[o].voxels() <= kTailMaxVoxels) {
-                pl.tail_start = o;
-                break;
-            }
+        for (int o = pl.nO - 1; o >= 1; --o) {
+            const OctaveGeom& g = pl.oct[o];
+            const int slab = (g.nz + kTailClusterPortable - 1) / kTailClusterPortable;
+            const bool fits = slab <= kTailMaxSlab && g.voxels() <= kTailMaxVoxels &&
+                              tail_smem_bytes(tail_row_pitch(g.nx) * g.ny, slab) <= kTailMaxSmem;
+            if (!fits) break;
+            pl.tail_start = o;
+        }
 
     size_t off = 0;
     for (int o = 0; o < pl.nO; ++o) {
@@ -240,32 +249,10 @@ int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, st
     ws->capacity = capacity;
     ws->base = base;
     ws->bytes = workspace_bytes(plan, capacity);
-    ws->tail_tasks = nullptr;
-    ws->tail_phase_begin = nullptr;
-    ws->tail_phases = 0;
     const size_t rec = round_up((size_t)std::max(capacity, 1) * sizeof(sift3d_keypoint), 256);
     ws->staging = reinterpret_cast<sift3d_keypoint*>(ws->base + plan.bytes);
     ws->count = reinterpret_cast<int*>(ws->base + plan.bytes + rec);
     ws->count_out = ws->count + 1;
-    if (plan.tail_start < plan.nO) {
-        std::vector<TailTask> tasks;
-        std::vector<int> begin;
-        build_tail_table(*ws, &tasks, &begin);
-        const size_t tb = tasks.size() * sizeof(TailTask), pb = begin.size() * sizeof(int);
-        void* mem = nullptr;
-        cudaError_t e = cudaMalloc(&mem, tb + pb);
-        if (e == cudaSuccess) e = cudaMemcpy(mem, tasks.data(), tb, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(static_cast<char*>(mem) + tb, begin.data(), pb, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            if (mem) cudaFree(mem);
-            (void)cudaGetLastError();
-            if (err) *err = std::string("octave-tail table: ") + cudaGetErrorString(e);
-            return e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
-        }
-        ws->tail_tasks = static_cast<TailTask*>(mem);
-        ws->tail_phase_begin = reinterpret_cast<int*>(static_cast<char*>(mem) + tb);
-        ws->tail_phases = (int)begin.size() - 1;
-    }
     return SIFT3D_OK;
 }
 
@@ -294,96 +281,60 @@ int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* 
 
 void free_workspace(Workspace* ws) {
     if (ws->base && ws->owns_base) cudaFree(ws->base);
-    if (ws->tail_tasks) cudaFree(ws->tail_tasks);
     ws->base = nullptr;
-    ws->tail_tasks = nullptr;
 }
 
-void build_tail_table(const Workspace& ws, std::vector<TailTask>* tasks, std::vector<int>* phase_begin) {
+TailArgs make_tail_args(const Workspace& ws) {
     const Plan& pl = ws.plan;
-    std::vector<std::vector<TailTask>> phases;
-    auto put = [&](int ph, TailTask t) {
-        if ((int)phases.size() <= ph) phases.resize(ph + 1);
-        t.n_tiles = tail_tiles(t);
-        if (t.n_tiles > 0) phases[ph].push_back(t);
-    };
-    for (int o = pl.tail_start; o < pl.nO; ++o) {
-        const OctaveGeom& g = pl.oct[o];
-        const int off = (o - pl.tail_start) * 2 * pl.S;   // the next octave starts 2S phases later
-        auto xy_args = [&](const void* src, int64_t spy, int64_t spz, float* dst, const Taps& taps) {
-            ConvXYArgs a{};
-            a.src = src;
-            a.src_py = spy;
-            a.src_pz = spz;
-            a.src_scale = 1.0f;
-            a.dst = dst;
-            a.py = g.py;
-            a.pz = g.pz;
-            a.nx = g.nx;
-            a.ny = g.ny;
-            a.nz = g.nz;
-            a.taps = taps;
-            return a;
-        };
-        auto z_args = [&](const float* src, void* dst, const void* prev, void* dog, const Taps& taps) {
-            ConvZArgs a{};
-            a.src = src;
-            a.dst = dst;
-            a.prev = prev;
-            a.dog = dog;
-            a.py = g.py;
-            a.pz = g.pz;
-            a.nx = g.nx;
-            a.ny = g.ny;
-            a.nz = g.nz;
-            a.taps = taps;
-            return a;
-        };
-        for (int s = 1; s < pl.L; ++s) {
-            TailTask t{};
-            t.radius = pl.r_inc[s - 1];
-            if (s == 1) {
-                t.type = TailTask::XY_SUB;
-                t.xy = xy_args(ws.G(o - 1, pl.S), pl.oct[o - 1].py, pl.oct[o - 1].pz, ws.T(o), pl.t_inc[0]);
-                t.xy.base_out = ws.G(o, 0);
-            } else {
-                t.type = TailTask::XY;
-                t.xy = xy_args(ws.G(o, s - 1), g.py, g.pz, ws.T(o), pl.t_inc[s - 1]);
-            }
-            put(off + 2 * (s - 1), t);
-            TailTask z{};
-            z.type = TailTask::Z;
-            z.radius = pl.r_inc[s - 1];
-            z.z = z_args(ws.T(o), ws.G(o, s), ws.G(o, s - 1), ws.D(o, s - 1), pl.t_inc[s - 1]);
-            put(off + 2 * (s - 1) + 1, z);
-            if (pl.r_desc > 0 && s <= pl.S) {   // pre-blur of G_s for the descriptors
-                TailTask b{};
-                b.type = TailTask::XY;
-                b.radius = pl.r_desc;
-                b.xy = xy_args(ws.G(o, s), g.py, g.pz, ws.TB(o, s), pl.t_desc);
-                put(off + 2 * s, b);
-                TailTask bz{};
-                bz.type = TailTask::Z;
-                bz.radius = pl.r_desc;
-                bz.z = z_args(ws.TB(o, s), ws.B(o, s), nullptr, nullptr, pl.t_desc);
-                put(off + 2 * s + 1, bz);
-            }
-        }
-        if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
-            TailTask t{};
-            t.type = TailTask::PEAK;
-            t.pk = make_peak_args(ws, o);
-            put(off + 2 * (pl.L - 1), t);
-        }
+    TailArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_oct = pl.nO - pl.tail_start;
+    a.L = pl.L;
+    a.S = pl.S;
+    const int prev = pl.tail_start - 1;
+    a.src = ws.G(prev, pl.S);
+    a.src_py = pl.oct[prev].py;
+    a.src_pz = pl.oct[prev].pz;
+    for (int s = 0; s + 1 < pl.L; ++s) {
+        a.r_inc[s] = pl.r_inc[s];
+        a.t_inc[s] = pl.t_inc[s];
     }
-    tasks->clear();
-    phase_begin->assign(1, 0);
-    for (auto& ph : phases) {
-        for (auto& t : ph) tasks->push_back(t);
-        phase_begin->push_back((int)tasks->size());
+    a.r_desc = pl.r_desc;
+    a.t_desc = pl.t_desc;
+    for (int i = 0; i < a.n_oct; ++i) a.max_nz = std::max(a.max_nz, pl.oct[pl.tail_start + i].nz);
+    for (int i = 0; i < a.n_oct; ++i) {
+        const int o = pl.tail_start + i;
+        TailOctave& t = a.oct[i];
+        t.nx = pl.oct[o].nx;
+        t.ny = pl.oct[o].ny;
+        t.nz = pl.oct[o].nz;
+        t.py = pl.oct[o].py;
+        t.pz = pl.oct[o].pz;
+        for (int s = 0; s < pl.L; ++s) t.G[s] = ws.G(o, s);
+        for (int s = 0; s < pl.nD; ++s) t.D[s] = ws.D(o, s);
+        for (int s = 1; s <= pl.S; ++s) t.B[s - 1] = ws.B(o, s);
     }
+    const int ncta = tail_cluster_size(pl.p.storage, a);
+    a.slab_planes = ncta > 0 ? (a.max_nz + ncta - 1) / ncta : 0;
+    return a;
 }
 
+cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st) {
+    if (s.cluster <= 0) return cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = s.grid;
+    cfg.blockDim = s.block;
+    cfg.dynamicSmemBytes = s.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)s.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, s.func, args);
+}
 
 PeakArgs make_peak_args(const Workspace& ws, int o) {
     const Plan& pl = ws.plan;
@@ -427,6 +378,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
+namespace {
+CUtensorMapDataType map_type(int storage) {
+    return storage == SIFT3D_STORAGE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+           : storage == SIFT3D_STORAGE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+}
+}  // namespace
+
 bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
     const Plan& pl = ws.plan;
     const OctaveGeom& g = pl.oct[o];
@@ -441,9 +400,7 @@ bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
         if (pl.off_D[o][s + 1] - pl.off_D[o][s] != stride) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc == nullptr) return false;
-    const CUtensorMapDataType dt = pl.p.storage == SIFT3D_STORAGE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : pl.p.storage == SIFT3D_STORAGE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = map_type(pl.p.storage);
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)pl.nD};
     const cuuint64_t strides[3] = {(cuuint64_t)g.py * pl.elem, (cuuint64_t)g.pz * pl.elem, (cuuint64_t)stride};
     const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)pl.nD};
@@ -472,6 +429,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         snprintf(buf, sizeof(buf), fmt, a, b, nodes[idx].spec.name);
         nodes[idx].label = buf;
         nodes[idx].algo_bytes = bytes;
+        nodes[idx].octave = a;
     };
     const uint64_t e = pl.elem;
     const uint64_t in_e = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 4;
@@ -479,7 +437,15 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
     bool fused[SIFT3D_MAX_OCTAVES][kMaxLevels] = {};
     *first_node = -1;
-    for (int o = 0; o < pl.tail_start; ++o) {
+    // the small-octave kernel runs when the device can hold its cluster;
+    // otherwise every octave takes the separate launches
+    TailArgs tail_args{};
+    int tail_start = pl.nO;
+    if (pl.tail_start < pl.nO) {
+        tail_args = make_tail_args(ws);
+        if (tail_args.slab_planes > 0) tail_start = pl.tail_start;
+    }
+    for (int o = 0; o < tail_start; ++o) {
         const OctaveGeom& g = pl.oct[o];
         int prev = -1;  // node that produced G_{s-1}
         for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
@@ -611,17 +577,26 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             }
         }
     }
-    if (pl.tail_start < pl.nO && ws.tail_tasks != nullptr) {
-        TailArgs ta{};
-        ta.tasks = ws.tail_tasks;
-        ta.phase_begin = ws.tail_phase_begin;
-        ta.n_phases = ws.tail_phases;
-        ta.bar = ws.count + 2;
-        ta.err = ws.count + 3;
-        const int tn = add(tail_spec(st, pl.S, kTailMaxCtas), ta, {g_node[pl.tail_start - 1][pl.S]});
-        nodes[tn].cooperative = true;
-        nodes[tn].label = "tail.o" + std::to_string(pl.tail_start) + "-" + std::to_string(pl.nO - 1);
-        peak_nodes.push_back(tn);
+    if (tail_start < pl.nO) {
+        // the pyramids of the small octaves in one cluster launch, then their
+        // peak detection as ordinary launches
+        const int tn = add(tail_spec(st, tail_args), tail_args, {g_node[tail_start - 1][pl.S]});
+        nodes[tn].label = "tail.o" + std::to_string(tail_start) + "-" + std::to_string(pl.nO - 1);
+        nodes[tn].octave = tail_start;
+        uint64_t tail_bytes = 0;
+        for (int o = tail_start; o < pl.nO; ++o)
+            tail_bytes += (uint64_t)((4.0 * pl.L - 2.875) * (double)pl.oct[o].voxels() * (double)pl.elem);
+        nodes[tn].algo_bytes = tail_bytes;
+        for (int o = tail_start; o < pl.nO; ++o) {
+            const OctaveGeom& g = pl.oct[o];
+            if (g.nx - 2 * pl.p.border < 1 || g.ny - 2 * pl.p.border < 1 || g.nz - 2 * pl.p.border < 1) continue;
+            PeakTmaArgs pa;
+            LaunchSpec ps;
+            if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
+            else ps.name = "peak (DoG tensor map)";
+            peak_nodes.push_back(add(ps, pa, {tn}));
+            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
+        }
     }
     SortArgs sa{};
     sa.staging = ws.staging;
@@ -635,6 +610,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     *sort_node = add(sort_spec(sa), sa, deps);
     tag(*sort_node, "o%d.x%d.%s", 0, 0, 0);
     nodes[*sort_node].label = "sort";
+    nodes[*sort_node].octave = -1;
     return nodes;
 }
 
@@ -786,9 +762,7 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             Node& n = ex.nodes[i];
             if (ex.profile) cudaEventRecord(ex.ev_begin[i], st);
-            cudaError_t e = n.cooperative
-                                ? cudaLaunchCooperativeKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st)
-                                : cudaLaunchKernel(n.spec.func, n.spec.grid, n.spec.block, &n.argp, n.spec.smem, st);
+            cudaError_t e = launch_spec(n.spec, &n.argp, st);
             if (e != cudaSuccess) return cuda_fail(err, n.spec.name, e);
             if (ex.profile) cudaEventRecord(ex.ev_end[i], st);
         }
@@ -798,10 +772,25 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         cudaError_t e = cudaGraphCreate(&ex.graph, 0);
         if (e != cudaSuccess) return cuda_fail(err, "cudaGraphCreate", e);
         ex.gnodes.resize(ex.nodes.size());
-        const bool pdl = ws.plan.p.use_pdl != 0 && !ex.profile;
+        // Programmatic (PDL) edges: use_pdl 1 = every kernel-to-kernel edge;
+        // 2 = only edges between kernels of octaves >= 1, whose small grids
+        // are latency bound and leave the SMs mostly free while they wait.
+        const int pdl_mode = ex.profile ? 0 : ws.plan.p.use_pdl;
+
+        auto programmatic = [&](int from, int to) {
+            const Node& a = ex.nodes[from];
+            const Node& b = ex.nodes[to];
+            if (pdl_mode == 0) return false;
+            if (pdl_mode == 1) return true;
+            return a.octave >= 1 && b.octave >= 1;
+        };
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             std::vector<cudaGraphNode_t> deps;
-            for (int d : ex.nodes[i].deps) deps.push_back(ex.gnodes[d]);
+            std::vector<int> prog_deps;
+            for (int d : ex.nodes[i].deps) {
+                if (programmatic(d, (int)i)) prog_deps.push_back(d);
+                else deps.push_back(ex.gnodes[d]);
+            }
             if (ex.profile) {   // begin event -> kernel -> end event
                 cudaGraphNode_t b;
                 e = cudaGraphAddEventRecordNode(&b, ex.graph, deps.data(), deps.size(), ex.ev_begin[i]);
@@ -809,28 +798,25 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
                 deps.assign(1, b);
             }
             cudaKernelNodeParams kp = node_params(ex.nodes[i]);
-            // With PDL, kernel-to-kernel edges are programmatic: the dependent
-            // launches while its predecessor drains and waits in griddepcontrol.
-            const bool prog = pdl && !ex.nodes[i].cooperative;
-            e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, prog ? nullptr : deps.data(), prog ? 0 : deps.size(),
-                                       &kp);
+            // A programmatic edge lets the dependent launch while its
+            // predecessor drains; it waits in griddepcontrol.wait.
+            e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, deps.data(), deps.size(), &kp);
             if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddKernelNode", e);
-            if (prog) {
-                for (int d : ex.nodes[i].deps) {
-                    cudaGraphEdgeData ed{};
-                    if (!ex.nodes[d].cooperative) {
-                        ed.from_port = cudaGraphKernelNodePortProgrammatic;
-                        ed.type = cudaGraphDependencyTypeProgrammatic;
-                    }
-                    e = cudaGraphAddDependencies(ex.graph, &ex.gnodes[d], &ex.gnodes[i], &ed, 1);
-                    if (e != cudaSuccess) return cuda_fail(err, "programmatic dependency", e);
-                }
+
+            for (int d : prog_deps) {
+                cudaGraphEdgeData ed{};
+                ed.from_port = cudaGraphKernelNodePortProgrammatic;
+                ed.type = cudaGraphDependencyTypeProgrammatic;
+                e = cudaGraphAddDependencies(ex.graph, &ex.gnodes[d], &ex.gnodes[i], &ed, 1);
+                if (e != cudaSuccess) return cuda_fail(err, "programmatic dependency", e);
             }
-            if (ex.nodes[i].cooperative) {
+            if (ex.nodes[i].spec.cluster > 0) {
                 cudaLaunchAttributeValue v{};
-                v.cooperative = 1;
-                e = cudaGraphKernelNodeSetAttribute(ex.gnodes[i], cudaLaunchAttributeCooperative, &v);
-                if (e != cudaSuccess) return cuda_fail(err, "cooperative kernel node", e);
+                v.clusterDim.x = (unsigned)ex.nodes[i].spec.cluster;
+                v.clusterDim.y = 1;
+                v.clusterDim.z = 1;
+                e = cudaGraphKernelNodeSetAttribute(ex.gnodes[i], cudaLaunchAttributeClusterDimension, &v);
+                if (e != cudaSuccess) return cuda_fail(err, "cluster kernel node", e);
             }
             if (ex.profile) {
                 cudaGraphNode_t en;

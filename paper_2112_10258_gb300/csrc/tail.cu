@@ -1,302 +1,401 @@
-// Octave-tail kernel for sm_103a: every octave after the first few runs inside
-// one cooperative launch.
+// Small-octave kernel for sm_103a: the whole pyramid of every small octave in
+// one launch of one thread-block cluster.
 //
-// Small octaves do little work per pass (octave 2 of a 145x174x145 volume has
-// 56K voxels), so as separate launches each pass costs mostly launch latency
-// and ramp-up.  Here the passes of the remaining octaves - y/x filtering, z
-// filtering with the DoG epilogue (Sec. 2.2.2), the descriptor pre-blur
-// (Sec. 2.2.3) and 4D peak detection - are tasks grouped into phases; the tiles
-// of all tasks of a phase are spread over the CTAs, and phases are separated by
-// a grid-wide barrier.  The next octave starts (from the sub-sampled level S)
-// in the same phase as level S+1 of the current one, so octaves overlap.
+// Octave o+1 starts from the sub-sampled level S of octave o (Sec. 2.2.2), so
+// the octaves form a chain of dependent passes.  Run as separate launches, each
+// pass of a small octave (octave 2 of a 145x174x145 volume has 56K voxels)
+// costs mostly launch latency, and the chain through octaves 1..3 outlasts the
+// bandwidth-bound work of octave 0.  Here the CLUSTER CTAs of one cluster own
+// contiguous z-slabs of the octave; every level of the slab stays in shared
+// memory:
+//   y pass   own planes of G_{s-1} (shared)       -> U  (shared)
+//   x pass   U                                    -> T  (shared, two buffers)
+//   cluster barrier
+//   z pass   T of this and the neighbouring CTAs  -> G_s (shared + global),
+//            read through distributed shared memory     D_{s-1} (global)
+// and the descriptor pre-blur B_s of G_s (Sec. 2.2.3) the same way.  T
+// alternates between two buffers, so one cluster barrier per pass suffices: a
+// CTA can only overwrite a T buffer after every CTA has passed the barrier that
+// follows the last read of it.  Every level, DoG and pre-blurred level is also
+// written to its place in the workspace, where the peak kernels, describe and
+// sift3d_read_level find it.
 //
-// The barrier waits are bounded: a CTA that waits longer than the spin limit
-// raises the error flag and returns, every other CTA sees the flag and returns,
-// and the detect reports the failure instead of hanging the device.
-//
-// Buffers are rewritten from phase to phase, so every load here is a plain
-// (coherent) load; the acquire side of the barrier orders them after the
-// previous phase's stores.
+// Every output is the same float32 chain as in the separate kernels (taps in
+// ascending k from 0, the 2x2x2 mean summed in the same order, levels rounded
+// to the storage type before they are filtered again), so the results are
+// bitwise those of the separate launches.  Cluster barriers are hardware
+// barriers: no spin loop here can run out.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
-#include "conv_tile.cuh"
-#include "peak_tile.cuh"
+#include "common.cuh"
 
 namespace sift3d {
 
 namespace {
 
-constexpr int TL_THREADS = 256;
-constexpr int TL_TX = conv_detail::XY_TX, TL_TY = conv_detail::XY_TY;   // y/x tile (64 x 32)
-constexpr int TL_ZC = TL_THREADS, TL_TZ = conv_detail::Z_TZ;           // z tile: 256 columns x 16 planes
-static_assert(conv_detail::XY_THREADS == TL_THREADS, "y/x tile body is written for 256 threads");
-constexpr unsigned kSpinLimit = 1u << 22; // about 0.3 s of polling
+namespace cg = cooperative_groups;
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+constexpr int CT = 512;               // threads per CTA
+constexpr int STRIP = 8;              // outputs per thread along the y and x passes
+constexpr int MAXP = kTailMaxSlab;    // planes per CTA slab
+
+// Taps of the pass being run, copied to shared memory so that strip functions
+// can hold them in registers by compile-time index.
+struct PassTaps {
+    float w[kMaxRadius + 1];
+};
+
+template <int R>
+__device__ __forceinline__ void load_taps(const PassTaps& t, float (&w)[R + 1]) {
+#pragma unroll
+    for (int k = 0; k <= R; ++k) w[k] = t.w[k];
 }
 
-// Grid barrier over a monotone counter.  Returns false when the wait ran out
-// (or another CTA already failed); the caller must then return.
-__device__ bool grid_barrier(int* counter, int* err, int target) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(counter, 1);
-        int good = 1;
-        for (unsigned spin = 0;; ++spin) {
-            if (ld_acquire(counter) >= target) break;
-            if (ld_acquire(err) != 0 || spin > kSpinLimit) {
-                atomicExch(err, 1);
-                good = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        ok = good;
+// y pass of one column strip: rows r0 .. r0+7 of column x of one plane.
+template <int R>
+__device__ __forceinline__ void y_strip(const float* src, float* dst, int py, int ny, int x, int r0,
+                                        const PassTaps& t) {
+    float w[R + 1];
+    load_taps<R>(t, w);
+    float v[STRIP + 2 * R];
+#pragma unroll
+    for (int i = 0; i < STRIP + 2 * R; ++i) v[i] = src[min(max(r0 - R + i, 0), ny - 1) * py + x];
+#pragma unroll
+    for (int j = 0; j < STRIP; ++j) {
+        if (r0 + j >= ny) break;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
+        dst[(r0 + j) * py + x] = acc;
+    }
+}
+
+// x pass of one row strip: columns c0 .. c0+7 of one row.
+template <int R>
+__device__ __forceinline__ void x_strip(const float* src, float* dst, int nx, int c0, const PassTaps& t) {
+    float w[R + 1];
+    load_taps<R>(t, w);
+    float v[STRIP + 2 * R];
+#pragma unroll
+    for (int i = 0; i < STRIP + 2 * R; ++i) v[i] = src[min(max(c0 - R + i, 0), nx - 1)];
+#pragma unroll
+    for (int j = 0; j < STRIP; ++j) {
+        if (c0 + j >= nx) break;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
+        dst[c0 + j] = acc;
+    }
+}
+
+// Geometry of the current octave as seen by one CTA.  The shared slabs use an
+// odd row pitch (nx | 1), so the lanes of a warp reading one column each (the x
+// pass walks rows) fall in distinct banks.
+struct Slab {
+    int nx, ny, nz;
+    int py, P;            // row pitch and plane size of the shared slabs
+    int z0, n;            // first plane and number of planes owned by this CTA
+    int rank, ncta;       // this CTA's rank and the cluster size
+};
+
+__device__ __forceinline__ int slab_begin(int k, int nz, int ncta) { return (k * nz) / ncta; }
+
+// y then x pass of the CTA's own planes: src (shared, float) -> dst (shared).
+// U is the scratch plane set between the passes.
+template <int R>
+__device__ void xy_pass(const Slab& g, const float* src, float* U, float* dst, const PassTaps& t) {
+    const int ystrips = (g.ny + STRIP - 1) / STRIP;
+    for (int i = threadIdx.x; i < g.n * g.nx * ystrips; i += CT) {
+        const int x = i % g.nx;
+        const int rest = i / g.nx;
+        const int rs = rest % ystrips, lz = rest / ystrips;
+        y_strip<R>(src + lz * g.P, U + lz * g.P, g.py, g.ny, x, rs * STRIP, t);
     }
     __syncthreads();
-    return ok != 0;
+    const int xstrips = (g.nx + STRIP - 1) / STRIP;
+    for (int i = threadIdx.x; i < g.n * g.ny * xstrips; i += CT) {
+        const int y = i % g.ny;            // lanes on consecutive rows: odd pitch, no bank conflict
+        const int rest = i / g.ny;
+        const int xs = rest % xstrips, lz = rest / xstrips;
+        x_strip<R>(U + lz * g.P + y * g.py, dst + lz * g.P + y * g.py, g.nx, xs * STRIP, t);
+    }
 }
 
-template <typename T>
-__device__ __forceinline__ float ldf(const T* p) { return to_f32(*p); }
-
-// y pass then x pass of one 64x32 tile of one plane, any radius R <= 16 (for
-// radii without a compiled register-window body).
-template <typename S>
-__device__ void xy_tile_generic(const ConvXYArgs& a, int R, bool sub, int tile, float* sm) {
-    const int tiles_x = (a.nx + TL_TX - 1) / TL_TX, tiles_y = (a.ny + TL_TY - 1) / TL_TY;
-    const int x0 = (tile % tiles_x) * TL_TX;
-    const int y0 = ((tile / tiles_x) % tiles_y) * TL_TY;
-    const int z = tile / (tiles_x * tiles_y);
-    const int W = TL_TX + 2 * R, H = TL_TY + 2 * R, WP = W | 1;
-    float* in = sm;
-    float* mid = sm + H * WP;
-    const S* src = static_cast<const S*>(a.src);
-    const int tid = threadIdx.x;
-#pragma unroll 4
-    for (int i = tid; i < H * W; i += TL_THREADS) {
-        const int r = i / W, c = i - (i / W) * W;
-        const int gy = min(max(y0 - R + r, 0), a.ny - 1);
-        const int gx = min(max(x0 - R + c, 0), a.nx - 1);
-        float v;
-        if (!sub) {
-            v = ldf(src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py + gx) * a.src_scale;
-        } else {
-            const S* p = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy) * a.src_py + 2 * gx;
+// z pass of the CTA's own planes from the T buffers of the cluster (this CTA
+// and its neighbours, through distributed shared memory).  For every output
+// voxel calls out(lz, shared offset in the plane, global offset in the plane,
+// value); gpy is the global row pitch.
+template <int R, class Out>
+__device__ void z_pass(const Slab& g, int64_t gpy, float* T, const PassTaps& t, const float** zplane, Out out) {
+    cg::cluster_group cluster = cg::this_cluster();
+    // Input plane q of this CTA's window is plane z = clamp(z0 - R + q) of the
+    // octave, held by the CTA k that owns z (the largest k with
+    // slab_begin(k) <= z, k = ceil((z+1) * ncta / nz) - 1).  The window's plane
+    // addresses are resolved once per pass.
+    if (threadIdx.x < g.n + 2 * R) {
+        const int z = min(max(g.z0 - R + (int)threadIdx.x, 0), g.nz - 1);
+        const int k = ((z + 1) * g.ncta + g.nz - 1) / g.nz - 1;
+        zplane[threadIdx.x] = cluster.map_shared_rank(T, k) + (z - slab_begin(k, g.nz, g.ncta)) * g.P;
+    }
+    __syncthreads();
+    float w[R + 1];
+    load_taps<R>(t, w);
+    const int cols = g.nx * g.ny;
+    for (int i = threadIdx.x; i < cols; i += CT) {
+        const int x = i % g.nx, y = i / g.nx;
+        const int off = y * g.py + x;
+        float v[MAXP + 2 * R];
+#pragma unroll
+        for (int q = 0; q < MAXP + 2 * R; ++q) v[q] = q < g.n + 2 * R ? zplane[q][off] : 0.f;
+        const int64_t goff = (int64_t)y * gpy + x;
+#pragma unroll
+        for (int j = 0; j < MAXP; ++j) {
+            if (j >= g.n) break;
             float acc = 0.f;
-            acc += ldf(p);
-            acc += ldf(p + 1);
-            acc += ldf(p + a.src_py);
-            acc += ldf(p + a.src_py + 1);
-            acc += ldf(p + a.src_pz);
-            acc += ldf(p + a.src_pz + 1);
-            acc += ldf(p + a.src_pz + a.src_py);
-            acc += ldf(p + a.src_pz + a.src_py + 1);
-            v = acc * 0.125f;
-            const int ty = r - R, tx = c - R;
-            if (ty >= 0 && ty < TL_TY && tx >= 0 && tx < TL_TX && y0 + ty < a.ny && x0 + tx < a.nx)
-                static_cast<S*>(a.base_out)[(int64_t)z * a.pz + (int64_t)(y0 + ty) * a.py + x0 + tx] = from_f32<S>(v);
+#pragma unroll
+            for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
+            out(j, off, goff, acc);
         }
-        in[r * WP + c] = v;
-    }
-    __syncthreads();
-    for (int i = tid; i < TL_TY * W; i += TL_THREADS) {
-        const int r = i / W, c = i - (i / W) * W;
-        float acc = 0.f;
-        for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], in[(r + R + k) * WP + c], acc);
-        mid[r * WP + c] = acc;
-    }
-    __syncthreads();
-    for (int i = tid; i < TL_TY * TL_TX; i += TL_THREADS) {
-        const int r = i / TL_TX, c = i - (i / TL_TX) * TL_TX;
-        const int y = y0 + r, x = x0 + c;
-        if (y >= a.ny || x >= a.nx) continue;
-        float acc = 0.f;
-        for (int k = -R; k <= R; ++k) acc = fmaf(a.taps.w[k < 0 ? -k : k], mid[r * WP + c + R + k], acc);
-        a.dst[(int64_t)z * a.pz + (int64_t)y * a.py + x] = acc;
     }
 }
 
-// z pass of 256 columns x 16 planes, any radius, with the optional DoG epilogue.
+// Dispatch on the radius (only radii of the schedule are ever hot).
+#define SIFT3D_RADIUS_SWITCH(R_RUNTIME, CALL)                          \
+    switch (R_RUNTIME) {                                              \
+        case 1: { constexpr int RR = 1; CALL; } break;                \
+        case 2: { constexpr int RR = 2; CALL; } break;                \
+        case 3: { constexpr int RR = 3; CALL; } break;                \
+        case 4: { constexpr int RR = 4; CALL; } break;                \
+        case 5: { constexpr int RR = 5; CALL; } break;                \
+        case 6: { constexpr int RR = 6; CALL; } break;                \
+        case 7: { constexpr int RR = 7; CALL; } break;                \
+        case 8: { constexpr int RR = 8; CALL; } break;                \
+        case 9: { constexpr int RR = 9; CALL; } break;                \
+        case 10: { constexpr int RR = 10; CALL; } break;              \
+        case 11: { constexpr int RR = 11; CALL; } break;              \
+        case 12: { constexpr int RR = 12; CALL; } break;              \
+        case 13: { constexpr int RR = 13; CALL; } break;              \
+        case 14: { constexpr int RR = 14; CALL; } break;              \
+        case 15: { constexpr int RR = 15; CALL; } break;              \
+        default: { constexpr int RR = 16; CALL; } break;              \
+    }
+
 template <typename S>
-__device__ void z_tile_generic(const ConvZArgs& a, int R, int tile) {
-    const int col_blocks = (int)((a.pz + TL_ZC - 1) / TL_ZC);
-    const int64_t col = (int64_t)(tile % col_blocks) * TL_ZC + threadIdx.x;
-    const int z0 = (tile / col_blocks) * TL_TZ;
-    if (col >= a.pz) return;
-    float acc[TL_TZ];
-#pragma unroll
-    for (int j = 0; j < TL_TZ; ++j) acc[j] = 0.f;
-    for (int k = -R; k <= R; ++k) {
-        const float w = a.taps.w[k < 0 ? -k : k];
-        float v[TL_TZ];
-#pragma unroll
-        for (int j = 0; j < TL_TZ; ++j) v[j] = a.src[(int64_t)min(max(z0 + j + k, 0), a.nz - 1) * a.pz + col];
-#pragma unroll
-        for (int j = 0; j < TL_TZ; ++j) acc[j] = fmaf(w, v[j], acc[j]);
-    }
-    float pv[TL_TZ];
-    if (a.dog != nullptr) {
-#pragma unroll
-        for (int j = 0; j < TL_TZ; ++j)
-            pv[j] = ldf(static_cast<const S*>(a.prev) + (int64_t)min(z0 + j, a.nz - 1) * a.pz + col);
-    }
-#pragma unroll
-    for (int j = 0; j < TL_TZ; ++j) {
-        const int z = z0 + j;
-        if (z >= a.nz) break;
-        const int64_t off = (int64_t)z * a.pz + col;
-        static_cast<S*>(a.dst)[off] = from_f32<S>(acc[j]);
-        if (a.dog != nullptr) static_cast<S*>(a.dog)[off] = from_f32<S>(pv[j] - acc[j]);
-    }
-}
+__device__ __forceinline__ float ld_s(const S* p) { return to_f32(*p); }
 
-// Radius dispatch: the radii of the default scale schedule (initial 7, then
-// 5 7 8 10 13, descriptor pre-blur 4) run the register-window bodies of the
-// conv kernels; any other radius runs the generic loops above.
-#define SIFT3D_TAIL_RADII(X) X(4) X(5) X(7) X(8) X(10) X(13)
-
-// Each tile body is a separate (not inlined) function so that it gets its own
-// register allocation; inlined into one kernel the bodies of all radii would
-// be allocated together and spill.
-template <int R, typename S, bool SUB, typename TB>
-__device__ __noinline__ void xy_call(const ConvXYArgs& a, int bx, int by, int z, float* sm) {
-    conv_detail::conv_xy_tile<R, S, SUB, TB>(a, bx, by, z, sm);
-}
-template <int R, typename S>
-__device__ __noinline__ void z_call(const ConvZArgs& a, int64_t col, int z0) {
-    conv_detail::conv_z_column<R, S, true, 0>(a, col, z0);
-}
+// 2x2x2 mean of the previous octave's level S at (2x, 2y, 2z), summed in the
+// same order as the separate sub-sampling pass.  The source may have been
+// written by this cluster: read at L2 (ld.cg), never through a stale L1 line.
 template <typename S>
-__device__ __noinline__ void peak_call(const PeakArgs& a, int bx, int by, int bz, float* fl, unsigned* surv, int* n) {
-    peak_detail::peak_tile<S>(a, bx, by, bz, fl, surv, *n);
+__device__ __forceinline__ float sub_mean_cg(const S* p, int64_t py, int64_t pz) {
+    auto g = [](const S* q) { return to_f32(__ldcg(q)); };
+    float acc = 0.f;
+    acc += g(p);
+    acc += g(p + 1);
+    acc += g(p + py);
+    acc += g(p + py + 1);
+    acc += g(p + pz);
+    acc += g(p + pz + 1);
+    acc += g(p + pz + py);
+    acc += g(p + pz + py + 1);
+    return acc * 0.125f;
 }
 
 template <typename S>
-__device__ __forceinline__ void run_xy(const TailTask& t, int local, float* sm) {
-    const ConvXYArgs& a = t.xy;
-    const int tiles_x = (a.nx + TL_TX - 1) / TL_TX, tiles_y = (a.ny + TL_TY - 1) / TL_TY;
-    const int bx = local % tiles_x, by = (local / tiles_x) % tiles_y, z = local / (tiles_x * tiles_y);
-    const bool sub = t.type == TailTask::XY_SUB;
-    if (sub) {   // only the first level of an octave sub-samples: radius 5 by default
-        if (t.radius == 5) xy_call<5, S, true, S>(a, bx, by, z, sm);
-        else xy_tile_generic<S>(a, t.radius, true, local, sm);
-        return;
-    }
-    switch (t.radius) {
-#define SIFT3D_XY_CASE(R)                                                    \
-    case R:                                                                   \
-        xy_call<R, S, false, float>(a, bx, by, z, sm);                        \
-        return;
-        SIFT3D_TAIL_RADII(SIFT3D_XY_CASE)
-#undef SIFT3D_XY_CASE
-        default:
-            xy_tile_generic<S>(a, t.radius, false, local, sm);
-    }
-}
+__global__ void __launch_bounds__(CT, 1) tail_kernel(const __grid_constant__ TailArgs a) {
+    extern __shared__ __align__(16) float tl_sm[];
+    __shared__ PassTaps taps;
+    __shared__ const float* zplane[MAXP + 2 * kMaxRadius];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int ncta = (int)cluster.num_blocks();
+    pdl_wait();   // level S of the octave before (no-op without a programmatic edge)
 
-template <typename S>
-__device__ __forceinline__ void run_z(const TailTask& t, int local) {
-    const ConvZArgs& a = t.z;
-    const int col_blocks = (int)((a.pz + TL_ZC - 1) / TL_ZC);
-    const int64_t col = (int64_t)(local % col_blocks) * TL_ZC + threadIdx.x;
-    const int z0 = (local / col_blocks) * TL_TZ;
-    switch (t.radius) {
-#define SIFT3D_Z_CASE(R)                                       \
-    case R:                                                     \
-        z_call<R, S>(a, col, z0);                               \
-        return;
-        SIFT3D_TAIL_RADII(SIFT3D_Z_CASE)
-#undef SIFT3D_Z_CASE
-        default:
-            z_tile_generic<S>(a, t.radius, local);
-    }
-}
+    for (int oi = 0; oi < a.n_oct; ++oi) {
+        const TailOctave& o = a.oct[oi];
+        Slab g;
+        g.nx = o.nx;
+        g.ny = o.ny;
+        g.nz = o.nz;
+        g.py = tail_row_pitch(o.nx);
+        g.P = g.py * o.ny;
+        g.rank = rank;
+        g.ncta = ncta;
+        g.z0 = slab_begin(rank, o.nz, ncta);
+        g.n = slab_begin(rank + 1, o.nz, ncta) - g.z0;
+        const int SL = a.slab_planes * g.P;         // floats per slab buffer
+        float* Gprev = tl_sm;
+        float* Gcur = tl_sm + SL;
+        float* U = tl_sm + 2 * SL;
+        float* Tb[2] = {tl_sm + 3 * SL, tl_sm + 4 * SL};
+        int tb = 0;
 
-template <typename S>
-__global__ void __launch_bounds__(TL_THREADS, 2) tail_kernel(const TailArgs t) {
-    extern __shared__ float tl_sm[];
-    for (int p = 0; p < t.n_phases; ++p) {
-        const int b = t.phase_begin[p], e = t.phase_begin[p + 1];
-        int total = 0;
-        for (int i = b; i < e; ++i) total += t.tasks[i].n_tiles;
-        for (int w = blockIdx.x; w < total; w += gridDim.x) {
-            int i = b, local = w;
-            while (local >= t.tasks[i].n_tiles) local -= t.tasks[i].n_tiles, ++i;
-            const TailTask& task = t.tasks[i];
-            switch (task.type) {
-                case TailTask::XY:
-                case TailTask::XY_SUB:
-                    run_xy<S>(task, local, tl_sm);
-                    break;
-                case TailTask::Z:
-                    run_z<S>(task, local);
-                    break;
-                case TailTask::PEAK: {
-                    const int ix = (task.pk.nx - 2 * task.pk.border + peak_detail::PK_BX - 1) / peak_detail::PK_BX;
-                    const int iy = (task.pk.ny - 2 * task.pk.border + peak_detail::PK_BY - 1) / peak_detail::PK_BY;
-                    float* fl = tl_sm;
-                    unsigned* surv = reinterpret_cast<unsigned*>(tl_sm + task.pk.n_scales * peak_detail::PK_LEVEL);
-                    int& n_surv = *reinterpret_cast<int*>(surv + peak_detail::PK_SURV);
-                    peak_call<S>(task.pk, local % ix, (local / ix) % iy, local / (ix * iy), fl, surv, &n_surv);
-                    break;
+        // ---- level 1 from the sub-sampled level S of the previous octave
+        {
+            const S* src = static_cast<const S*>(oi == 0 ? a.src : a.oct[oi - 1].G[a.S]);
+            const int64_t spy = oi == 0 ? a.src_py : a.oct[oi - 1].py;
+            const int64_t spz = oi == 0 ? a.src_pz : a.oct[oi - 1].pz;
+            S* G0 = static_cast<S*>(o.G[0]);
+            // Gprev <- G_0 rounded to the storage type (it is what D_0 uses and
+            // what the separate path stores); Gcur <- the unrounded mean, which
+            // the separate path filters.
+            // Batches of NB voxels per thread: all 8 * NB loads are issued
+            // before the first store, so a thread waits for L2 once per batch.
+            constexpr int NB = 8;
+            const int nvox = g.n * g.nx * g.ny;
+            for (int base = 0; base < nvox; base += NB * CT) {
+                float m[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int i = base + b * CT + threadIdx.x;
+                    m[b] = 0.f;
+                    if (i < nvox) {
+                        const int x = i % g.nx;
+                        const int rest = i / g.nx;
+                        const int y = rest % g.ny, z = g.z0 + rest / g.ny;
+                        m[b] = sub_mean_cg<S>(src + (int64_t)(2 * z) * spz + (int64_t)(2 * y) * spy + 2 * x, spy, spz);
+                    }
                 }
-                default:
-                    break;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const int i = base + b * CT + threadIdx.x;
+                    if (i < nvox) {
+                        const int x = i % g.nx;
+                        const int rest = i / g.nx;
+                        const int y = rest % g.ny, lz = rest / g.ny;
+                        const S ms = from_f32<S>(m[b]);
+                        G0[(int64_t)(g.z0 + lz) * o.pz + (int64_t)y * o.py + x] = ms;
+                        Gprev[lz * g.P + y * g.py + x] = to_f32(ms);
+                        Gcur[lz * g.P + y * g.py + x] = m[b];
+                    }
+                }
             }
-            __syncthreads();   // shared memory is reused by the next tile
         }
-        if (p + 1 < t.n_phases && !grid_barrier(t.bar, t.err, (p + 1) * (int)gridDim.x)) return;
+        for (int s = 1; s < a.L; ++s) {
+            if (threadIdx.x <= kMaxRadius) taps.w[threadIdx.x] = a.t_inc[s - 1].w[threadIdx.x];
+            __syncthreads();
+            float* T = Tb[tb];
+            const int R = a.r_inc[s - 1];
+            // level 1 filters the unrounded mean held in Gcur, later levels G_{s-1}
+            const float* xsrc = s == 1 ? Gcur : Gprev;
+            SIFT3D_RADIUS_SWITCH(R, (xy_pass<RR>(g, xsrc, U, T, taps)));
+            cluster.sync();
+            S* Gs = static_cast<S*>(o.G[s]);
+            S* Ds = static_cast<S*>(o.D[s - 1]);
+            const int64_t zoff = (int64_t)g.z0 * o.pz;
+            SIFT3D_RADIUS_SWITCH(R, (z_pass<RR>(g, o.py, T, taps, zplane,
+                                                [&](int j, int off, int64_t goff, float acc) {
+                                                    const S gs = from_f32<S>(acc);
+                                                    const int li = j * g.P + off;
+                                                    Gs[zoff + (int64_t)j * o.pz + goff] = gs;
+                                                    Ds[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(Gprev[li] - acc);
+                                                    Gcur[li] = to_f32(gs);
+                                                })));
+            __syncthreads();
+            float* t = Gprev;   // G_s becomes the next level's source
+            Gprev = Gcur;
+            Gcur = t;
+            tb ^= 1;
+            // descriptor pre-blur of G_s, s = 1..S
+            if (a.r_desc > 0 && s <= a.S) {
+                if (threadIdx.x <= kMaxRadius) taps.w[threadIdx.x] = a.t_desc.w[threadIdx.x];
+                __syncthreads();
+                float* T2 = Tb[tb];
+                SIFT3D_RADIUS_SWITCH(a.r_desc, (xy_pass<RR>(g, Gprev, U, T2, taps)));
+                cluster.sync();
+                S* Bs = static_cast<S*>(o.B[s - 1]);
+                SIFT3D_RADIUS_SWITCH(a.r_desc, (z_pass<RR>(g, o.py, T2, taps, zplane,
+                                                           [&](int j, int, int64_t goff, float acc) {
+                                                               Bs[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(acc);
+                                                           })));
+                __syncthreads();
+                tb ^= 1;
+            }
+        }
+        // the next octave sub-samples this octave's level S, written by every
+        // CTA: all stores before this barrier are visible after it
+        cluster.sync();
     }
 }
 
 }  // namespace
 
-int tail_smem_bytes(int n_scales) {
-    const int xy = conv_detail::XYGeom<kMaxRadius>::SMEM;
-    const int pk = peak_detail::peak_smem_bytes(n_scales) + peak_detail::PK_SURV * 4 + 16;
-    return std::max(xy, pk);
-}
-
-int tail_tiles(const TailTask& t) {
-    switch (t.type) {
-        case TailTask::XY:
-        case TailTask::XY_SUB:
-            return ((t.xy.nx + TL_TX - 1) / TL_TX) * ((t.xy.ny + TL_TY - 1) / TL_TY) * t.xy.nz;
-        case TailTask::Z:
-            return (int)((t.z.pz + TL_ZC - 1) / TL_ZC) * ((t.z.nz + TL_TZ - 1) / TL_TZ);
-        case TailTask::PEAK: {
-            const int b = t.pk.border;
-            return ((t.pk.nx - 2 * b + peak_detail::PK_BX - 1) / peak_detail::PK_BX) *
-                   ((t.pk.ny - 2 * b + peak_detail::PK_BY - 1) / peak_detail::PK_BY) *
-                   ((t.pk.nz - 2 * b + peak_detail::PK_TZ - 1) / peak_detail::PK_TZ);
+// Cluster size for the small-octave kernel: 16 CTAs where the device can
+// schedule such a cluster with this shared memory, else the portable 8.
+static int pick_cluster(const void* func, const TailArgs& a, size_t* smem_out) {
+    int max_plane = 0, max_nz = 0;
+    for (int i = 0; i < a.n_oct; ++i) {
+        max_plane = std::max(max_plane, tail_row_pitch(a.oct[i].nx) * a.oct[i].ny);
+        max_nz = std::max(max_nz, a.oct[i].nz);
+    }
+    for (int ncta : {kTailCluster, kTailClusterPortable}) {
+        const int slab = (max_nz + ncta - 1) / ncta;
+        if (slab > kTailMaxSlab) continue;
+        const size_t smem = tail_smem_bytes(max_plane, slab);
+        if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (ncta > 8 && cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(ncta, 1, 1);
+        cfg.blockDim = dim3(CT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = ncta;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, func, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (n >= 1) {
+            *smem_out = smem;
+            return ncta;
         }
     }
     return 0;
 }
 
-LaunchSpec tail_spec(int storage, int n_scales, int max_ctas) {
+LaunchSpec tail_spec(int storage, const TailArgs& a) {
     LaunchSpec s;
     if (storage == SIFT3D_STORAGE_F32) s.func = reinterpret_cast<const void*>(&tail_kernel<float>);
     else if (storage == SIFT3D_STORAGE_F16) s.func = reinterpret_cast<const void*>(&tail_kernel<__half>);
     else s.func = reinterpret_cast<const void*>(&tail_kernel<__nv_bfloat16>);
-    s.smem = tail_smem_bytes(n_scales);
-    if (s.smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.func, TL_THREADS, s.smem);
-    const int fit = std::max(1, sms * std::max(per_sm, 1));
-    s.grid = dim3((unsigned)std::min(max_ctas * 2, fit));
-    s.block = dim3(TL_THREADS);
+    size_t smem = 0;
+    const int ncta = pick_cluster(s.func, a, &smem);
+    if (ncta == 0 || a.slab_planes != (a.max_nz + ncta - 1) / ncta) {
+        s.func = nullptr;
+        s.name = "tail (cluster)";
+        return s;
+    }
+    s.grid = dim3(ncta, 1, 1);
+    s.block = dim3(CT);
+    s.smem = smem;
+    s.cluster = ncta;
     s.name = "tail";
     return s;
+}
+
+int tail_cluster_size(int storage, const TailArgs& a) {
+    const void* f = storage == SIFT3D_STORAGE_F32   ? reinterpret_cast<const void*>(&tail_kernel<float>)
+                    : storage == SIFT3D_STORAGE_F16 ? reinterpret_cast<const void*>(&tail_kernel<__half>)
+                                                    : reinterpret_cast<const void*>(&tail_kernel<__nv_bfloat16>);
+    size_t smem = 0;
+    return pick_cluster(f, a, &smem);
+}
+
+size_t tail_smem_bytes(int plane_elems, int slab_planes) {
+    return (size_t)5 * slab_planes * plane_elems * sizeof(float);
 }
 
 }  // namespace sift3d

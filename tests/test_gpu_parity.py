@@ -220,8 +220,9 @@ def test_gaussian_blur_matches_oracle(S, shape, sigma):
 
 @pytest.mark.parametrize("shape", [(145, 174, 145), (64, 64, 64), (100, 90, 80)])
 def test_octave_tail_kernel_equals_separate_launches(S, shape):
-    """Octaves after the first run in one cooperative launch by default; the
-    result must be bitwise the same as launching every pass separately."""
+    """With fuse_small_octaves the last small octaves build their pyramids in
+    one thread-block-cluster launch; every level, DoG, pre-blurred level,
+    keypoint and descriptor must be bitwise what separate launches give."""
     vol = brain_like_volume(seed=6, shape=shape)
     outs = []
     for fuse in (0, 1):
