@@ -541,8 +541,8 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
             else ps.name = "peak (DoG tensor map)";
             peak_nodes.push_back(add(ps, pa, {g_node[o][pl.L - 1]}));
-            // D_1..D_S must be read in full; D_0 and D_{S+1} only around candidates
-            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
+            // the 80-neighbour test reads every DoG level D_0..D_{S+1} in full
+            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * e * (uint64_t)g.voxels());
         }
         // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3), where no level
         // pass fused it
@@ -595,7 +595,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
             else ps.name = "peak (DoG tensor map)";
             peak_nodes.push_back(add(ps, pa, {tn}));
-            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.S * e * (uint64_t)g.voxels());
+            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * e * (uint64_t)g.voxels());
         }
     }
     SortArgs sa{};
