@@ -187,7 +187,7 @@ def cpu_baseline(vol):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("conv.cu", "peak.cu", "describe.cu", "common.cuh"):
+    for f in ("conv.cu", "conv_tile.cuh", "peak.cu", "tma.cuh", "describe.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2112_10258_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
