@@ -386,7 +386,7 @@ def sort_keypoints(kps: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------
-# Point-pair pattern (Sec. 2.2.3, method 3) from SplitMix64 + Box-Muller
+# Point-pair patterns (Sec. 2.2.3, methods 1-5) from SplitMix64 + Box-Muller
 # ----------------------------------------------------------------------------------
 
 MASK64 = (1 << 64) - 1
@@ -439,6 +439,90 @@ def pattern_method3(seed: int, n_pairs: int = N_PAIRS, clip: float = PATTERN_CLI
                 break
         out[k, 0], out[k, 1] = p1, p2
     return out
+
+
+def _normal_point(rng: NormalStream, mean: np.ndarray, clip: float) -> np.ndarray:
+    """mean + N(0, I), redrawn until every |coordinate| <= clip."""
+    while True:
+        q = mean + np.array([rng.normal() for _ in range(3)])
+        if np.all(np.abs(q) <= clip):
+            return q
+
+
+def pattern_method1(seed: int, n_pairs: int = N_PAIRS, radius: float = 2.0) -> np.ndarray:
+    """Method 1 (Sec. 2.2.3): p1 and p2 uniform in the ball of radius 2 sigma (the
+    paper's 2D circle, in 3D), in units of the keypoint scale.  Each point is
+    three uniforms on (-radius, radius) from the SplitMix64 stream, redrawn until
+    it lies inside the ball.  Returns (n_pairs, 2, 3) in (x, y, z)."""
+    rng = NormalStream(seed)
+
+    def point():
+        while True:
+            q = np.array([radius * (2.0 * rng.uniform() - 1.0) for _ in range(3)])
+            if q @ q <= radius * radius:
+                return q
+
+    out = np.zeros((n_pairs, 2, 3))
+    for k in range(n_pairs):
+        out[k, 0] = point()
+        out[k, 1] = point()
+    return out
+
+
+def pattern_method2(seed: int, n_pairs: int = N_PAIRS, clip: float = PATTERN_CLIP) -> np.ndarray:
+    """Method 2 (Sec. 2.2.3): p1 and p2 independent, each N(0, sigma) (keypoint-scale
+    units); a point with any |coordinate| > clip is redrawn."""
+    rng = NormalStream(seed)
+    out = np.zeros((n_pairs, 2, 3))
+    for k in range(n_pairs):
+        out[k, 0] = _normal_point(rng, np.zeros(3), clip)
+        out[k, 1] = _normal_point(rng, np.zeros(3), clip)
+    return out
+
+
+def pattern_method4(seed: int, n_pairs: int = N_PAIRS, clip: float = PATTERN_CLIP) -> np.ndarray:
+    """Method 4 (Sec. 2.2.3, the paper's new method): p1 at the patch centre, p2 ~
+    N(0, sigma) (keypoint-scale units), redrawn if any |coordinate| > clip."""
+    rng = NormalStream(seed)
+    out = np.zeros((n_pairs, 2, 3))
+    for k in range(n_pairs):
+        out[k, 1] = _normal_point(rng, np.zeros(3), clip)
+    return out
+
+
+POLAR_RADII = (0.5, 1.0, 1.5, 2.0)       # keypoint-scale units
+POLAR_COS_THETA = (0.75, 0.25, -0.25, -0.75)
+
+
+def pattern_method5(n_pairs: int = N_PAIRS) -> np.ndarray:
+    """Method 5 (Sec. 2.2.3): p1 at the patch centre, p2 on a regular polar grid,
+    read in 3D as spherical coordinates: 4 radii (0.5, 1, 1.5, 2 sigma) x 4 rings
+    equally spaced in cos(theta) (0.75, 0.25, -0.25, -0.75) x 4 azimuths
+    phi = pi/2 * a, rotated by pi/4 on odd rings.  Pair 16 m + 4 j + a has radius
+    m, ring j, azimuth a.  Deterministic (no seed)."""
+    out = np.zeros((n_pairs, 2, 3))
+    for k in range(n_pairs):
+        m, j, az = (k // 16) % 4, (k // 4) % 4, k % 4
+        r, ct = POLAR_RADII[m], POLAR_COS_THETA[j]
+        st = math.sqrt(1.0 - ct * ct)
+        phi = 0.5 * math.pi * az + (0.25 * math.pi if j % 2 == 1 else 0.0)
+        out[k, 1] = [r * st * math.cos(phi), r * st * math.sin(phi), r * ct]
+    return out
+
+
+def pattern_for(p: "Params") -> np.ndarray:
+    """The point-pair pattern of p.desc_method (1..5) and p.pattern_seed."""
+    if p.desc_method == 1:
+        return pattern_method1(p.pattern_seed)
+    if p.desc_method == 2:
+        return pattern_method2(p.pattern_seed)
+    if p.desc_method == 3:
+        return pattern_method3(p.pattern_seed)
+    if p.desc_method == 4:
+        return pattern_method4(p.pattern_seed)
+    if p.desc_method == 5:
+        return pattern_method5()
+    raise ValueError("desc_method must be 1..5")
 
 
 # ----------------------------------------------------------------------------------
@@ -495,7 +579,7 @@ def blurred_level(pyr: Pyramid, o: int, s: int, p: Params) -> np.ndarray:
 def describe(pyr: Pyramid, kps: np.ndarray, p: Params, pattern: np.ndarray | None = None,
              cache: dict | None = None) -> DescribeResult:
     if pattern is None:
-        pattern = pattern_method3(p.pattern_seed)
+        pattern = pattern_for(p)
     n = kps.size
     npair = pattern.shape[0]
     d = np.zeros((n, npair))

@@ -363,6 +363,55 @@ def test_pattern_method3_properties():
     assert abs(np.corrcoef(p1.ravel(), d.ravel())[0, 1]) < 0.1
 
 
+def test_pattern_method1_uniform_ball():
+    P = O.pattern_method1(7)
+    assert P.shape == (64, 2, 3)
+    assert np.all(np.sum(P * P, axis=2) <= 4.0)                           # inside the radius-2 ball
+    pts = np.concatenate([O.pattern_method1(sd).reshape(-1, 3) for sd in range(40)])
+    r = np.sqrt(np.sum(pts * pts, axis=1))
+    # uniform in a ball of radius R: P(r <= t) = (t/R)^3, E[r] = 3R/4, E[r^2] = 3R^2/5
+    assert abs(r.mean() - 1.5) < 0.03 and abs(np.mean(r * r) - 2.4) < 0.06
+    assert abs(np.mean(r <= 1.0) - 0.125) < 0.02
+    assert abs(pts.mean()) < 0.05
+    assert not np.array_equal(O.pattern_method1(7), O.pattern_method1(8))
+
+
+def test_pattern_method2_independent_normals():
+    pts = np.concatenate([O.pattern_method2(sd) for sd in range(40)])
+    p1, p2 = pts[:, 0, :], pts[:, 1, :]
+    assert np.all(np.abs(pts) <= 4.0)
+    for q in (p1, p2):
+        assert abs(q.mean()) < 0.06 and abs(q.std() - 1.0) < 0.06
+    assert abs(np.corrcoef(p1.ravel(), p2.ravel())[0, 1]) < 0.1            # independent, unlike method 3
+
+
+def test_pattern_method4_centre_and_normal():
+    pts = np.concatenate([O.pattern_method4(sd) for sd in range(40)])
+    assert np.all(pts[:, 0, :] == 0.0)                                     # p1 at the centre
+    p2 = pts[:, 1, :]
+    assert abs(p2.mean()) < 0.06 and abs(p2.std() - 1.0) < 0.06
+
+
+def test_pattern_method5_polar_grid():
+    P = O.pattern_method5()
+    assert np.all(P[:, 0, :] == 0.0)
+    r = np.sqrt(np.sum(P[:, 1, :] ** 2, axis=1))
+    np.testing.assert_allclose(np.sort(np.unique(np.round(r, 12))), [0.5, 1.0, 1.5, 2.0], atol=1e-12)
+    for m, rad in enumerate((0.5, 1.0, 1.5, 2.0)):
+        np.testing.assert_allclose(r[16 * m: 16 * m + 16], rad, atol=1e-12)
+    u = P[:16, 1, :] / 0.5                                                 # 16 distinct unit directions
+    assert len({tuple(np.round(v, 9)) for v in u}) == 16
+    np.testing.assert_allclose(u.sum(axis=0), 0.0, atol=1e-12)            # the grid is balanced
+    np.testing.assert_allclose(np.sort(np.unique(np.round(u[:, 2], 12))), [-0.75, -0.25, 0.25, 0.75])
+
+
+def test_pattern_for_dispatches_each_method():
+    for m, fn in ((1, O.pattern_method1), (2, O.pattern_method2), (3, O.pattern_method3), (4, O.pattern_method4)):
+        p = O.Params(desc_method=m, pattern_seed=99)
+        np.testing.assert_array_equal(O.pattern_for(p), fn(99))
+    np.testing.assert_array_equal(O.pattern_for(O.Params(desc_method=5)), O.pattern_method5())
+
+
 # ------------------------------------------------------------------ descriptors
 
 
