@@ -604,3 +604,49 @@ def describe(pyr: Pyramid, kps: np.ndarray, p: Params, pattern: np.ndarray | Non
         brief |= bits[:, k] << np.uint64(k)
     rrief = rank_order(d).astype(np.uint8)
     return DescribeResult(brief, rrief, d, mag)
+
+
+# ----------------------------------------------------------------------------------
+# Matching (Sec. 2.1 (e)): nearest neighbour of each descriptor of A among B
+# ----------------------------------------------------------------------------------
+
+def hamming_distances(brief_a: np.ndarray, brief_b: np.ndarray) -> np.ndarray:
+    """(na, nb) number of differing bits between the 64-bit BRIEF words."""
+    x = brief_a.astype(np.uint64)[:, None] ^ brief_b.astype(np.uint64)[None, :]
+    bits = (x[..., None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)
+    return bits.sum(axis=-1).astype(np.int64)
+
+
+def rank_distances(rrief_a: np.ndarray, rrief_b: np.ndarray) -> np.ndarray:
+    """(na, nb) squared Euclidean distance between RRIEF rank vectors,
+    sum_k (r_a[k] - r_b[k])^2."""
+    a = rrief_a.astype(np.int64)
+    b = rrief_b.astype(np.int64)
+    return ((a[:, None, :] - b[None, :, :]) ** 2).sum(axis=-1)
+
+
+def nearest_neighbours(dist: np.ndarray):
+    """For each row: the index of the smallest distance (the lowest index among
+    equal ones), that distance, and the smallest distance over the other
+    columns (the second nearest; INT32_MAX if there is none).  An empty row set
+    of columns gives index -1 and INT32_MAX distances."""
+    na, nb = dist.shape
+    big = 2 ** 31 - 1
+    nn = np.full(na, -1, np.int64)
+    d1 = np.full(na, big, np.int64)
+    d2 = np.full(na, big, np.int64)
+    for i in range(na):
+        if nb == 0:
+            continue
+        j = int(np.argmin(dist[i]))          # first occurrence: lowest index
+        nn[i], d1[i] = j, dist[i, j]
+        if nb > 1:
+            d2[i] = np.min(np.delete(dist[i], j))
+    return nn, d1, d2
+
+
+def match(desc_a: np.ndarray, desc_b: np.ndarray, kind: int):
+    """kind 1 = BRIEF (uint64 words, Hamming distance), 2 = RRIEF ((n, 64) ranks,
+    squared rank distance).  Returns nearest_neighbours of the distance matrix."""
+    d = hamming_distances(desc_a, desc_b) if kind == 1 else rank_distances(desc_a, desc_b)
+    return nearest_neighbours(d)

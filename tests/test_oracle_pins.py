@@ -506,3 +506,48 @@ def test_rrief_is_permutation_and_brief_bit_layout():
     for i in range(d.d.shape[0]):
         for kbit in range(64):
             assert ((int(d.brief[i]) >> kbit) & 1) == int(d.d[i, kbit] > 0)
+
+
+# ------------------------------------------------------------------ matching
+
+
+def test_hamming_distance_counts_bits():
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 2 ** 63, 7, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, 7, dtype=np.uint64)
+    b = rng.integers(0, 2 ** 63, 5, dtype=np.uint64)
+    D = O.hamming_distances(a, b)
+    for i in range(7):
+        for j in range(5):
+            assert D[i, j] == bin(int(a[i]) ^ int(b[j])).count("1")
+    assert O.hamming_distances(np.array([0], np.uint64), np.array([2 ** 64 - 1], np.uint64))[0, 0] == 64
+
+
+def test_rank_distance_matches_spearman():
+    # for permutations of 0..n-1: sum (a-b)^2 = n (n^2 - 1) / 6 * (1 - rho_spearman)
+    from scipy.stats import spearmanr
+    rng = np.random.default_rng(4)
+    A = np.array([rng.permutation(64) for _ in range(6)], np.uint8)
+    B = np.array([rng.permutation(64) for _ in range(4)], np.uint8)
+    D = O.rank_distances(A, B)
+    for i in range(6):
+        for j in range(4):
+            rho = spearmanr(A[i], B[j]).statistic
+            assert abs(D[i, j] - 64 * (64 ** 2 - 1) / 6 * (1 - rho)) < 1e-6
+    assert O.rank_distances(A[:1], A[:1])[0, 0] == 0
+    assert O.rank_distances(np.arange(64, dtype=np.uint8)[None], np.arange(63, -1, -1, dtype=np.uint8)[None])[0, 0] \
+        == 2 * 64 * (64 ** 2 - 1) // 6                                     # reversed order: rho = -1
+
+
+def test_nearest_neighbours_ties_and_edges():
+    D = np.array([[5, 3, 3, 9], [0, 0, 0, 0], [7, 8, 9, 1]])
+    nn, d1, d2 = O.nearest_neighbours(D)
+    assert nn.tolist() == [1, 0, 3] and d1.tolist() == [3, 0, 1] and d2.tolist() == [3, 0, 7]
+    nn, d1, d2 = O.nearest_neighbours(np.zeros((2, 1), np.int64))
+    assert nn.tolist() == [0, 0] and d2.tolist() == [2 ** 31 - 1] * 2
+    nn, d1, d2 = O.nearest_neighbours(np.zeros((3, 0), np.int64))
+    assert nn.tolist() == [-1] * 3 and d1.tolist() == [2 ** 31 - 1] * 3
+    # a descriptor set matched against itself finds itself at distance 0
+    rng = np.random.default_rng(5)
+    W = rng.integers(0, 2 ** 63, 20, dtype=np.uint64)
+    nn, d1, _ = O.match(W, W, 1)
+    assert nn.tolist() == list(range(20)) and not d1.any()
