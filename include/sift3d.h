@@ -109,7 +109,12 @@ typedef struct sift3d_params {
     double   curvature_r;        /* 10, > 1                                    */
     double   trunc;              /* 4.0  filter radius = ceil(trunc * sigma)   */
     double   desc_blur_sigma;    /* 0.95; 0 = sample G_s without pre-blur     */
-    int32_t  desc_method;        /* 3 (p1 ~ N(0,1), p2 ~ N(p1,1))              */
+    int32_t  desc_method;        /* point pairs (Sec. 2.2.3), keypoint-scale
+                                    units: 1 = both uniform in the ball of
+                                    radius 2; 2 = both N(0,1); 3 (default) =
+                                    p1 ~ N(0,1), p2 ~ N(p1,1); 4 = p1 = 0,
+                                    p2 ~ N(0,1); 5 = p1 = 0, p2 on a spherical
+                                    grid (4 radii x 16 directions)            */
     uint64_t pattern_seed;       /* seeds the SplitMix64 pattern generator     */
     int32_t  storage;            /* SIFT3D_STORAGE_*                           */
     int32_t  use_graphs;         /* 1 = replay detect as a captured CUDA graph */
@@ -185,10 +190,19 @@ int sift3d_plan(const sift3d_params* params, int nx, int ny, int nz,
 
 /* Write the 64 point pairs the descriptors use, as float
  * out[k*6 + p*3 + c] (pair k, point p in {0,1}, coordinate c = x,y,z), in units
- * of the keypoint's scale.  Method 3 (Sec. 2.2.3): p1 ~ N(0,1), p2 ~ N(p1,1)
- * per coordinate, a point with any |coordinate| > 4 redrawn; normals from
- * SplitMix64 (seeded with pattern_seed) through Box-Muller, one cos branch per
- * pair of uniforms.  Host only. */
+ * of the keypoint's scale, for params->desc_method (Sec. 2.2.3, point selection
+ * methods 1-5):
+ *   1  p1, p2 uniform in the ball of radius 2 (three uniforms on (-2, 2) per
+ *      point, redrawn until inside);
+ *   2  p1, p2 ~ N(0,1) per coordinate;
+ *   3  p1 ~ N(0,1), p2 ~ N(p1,1) per coordinate;
+ *   4  p1 = 0, p2 ~ N(0,1);
+ *   5  p1 = 0, p2 = r (sin t cos f, sin t sin f, cos t) with pair 16m + 4j + a:
+ *      r = 0.5 (m+1), cos t = 0.75 - 0.5 j, f = pi/2 a + (j odd ? pi/4 : 0).
+ * A normal point with any |coordinate| > 4 is redrawn.  Uniforms and normals
+ * come from SplitMix64 seeded with pattern_seed (normals by Box-Muller, one cos
+ * branch per pair of uniforms); method 5 uses no random numbers.  Host only.
+ * SIFT3D_EINVAL on bad params. */
 int sift3d_pattern(const sift3d_params* params, float* out);
 
 /* Create a context.  Validates params (SIFT3D_EINVAL) and stores them; device
@@ -275,6 +289,26 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
 #define SIFT3D_BLUR_NOALLOC_MAX_ELEMS (1 << 22)
 int sift3d_gaussian_blur_noalloc(const float* dev_in, int nx, int ny, int nz, double sigma,
                                  double trunc, float* dev_out, void* stream);
+
+/* Nearest-neighbour matching of descriptors (Sec. 2.1 (e): descriptors are
+ * matched by nearest neighbour).  For each descriptor i of set A the call
+ * finds, by brute force over set B:
+ *   dev_nn[i]     index of the nearest descriptor in B (the lowest index among
+ *                 equal distances), -1 if nb == 0;
+ *   dev_dist[i]   its distance, INT32_MAX if nb == 0;
+ *   dev_dist2[i]  the smallest distance to any other descriptor of B (the
+ *                 second nearest, for a ratio test), INT32_MAX if nb < 2; may be
+ *                 NULL.
+ * kind SIFT3D_DESC_BRIEF: A and B are uint64 words as sift3d_describe writes
+ *   them (8-byte aligned); the distance is the Hamming distance, 0..64.
+ * kind SIFT3D_DESC_RRIEF: A and B are rows of 64 uint8 ranks (16-byte aligned,
+ *   row i at byte 64 i); the distance is sum_k (a_k - b_k)^2, exact.
+ * All pointers are device memory owned by the caller; the call allocates
+ * nothing and is ordered on `stream`.  na == 0 launches nothing.
+ * Errors: SIFT3D_EINVAL (kind, negative counts, NULL or misaligned pointers),
+ * SIFT3D_ECUDA. */
+int sift3d_match(const void* dev_a, int na, const void* dev_b, int nb, int kind, int32_t* dev_nn,
+                 int32_t* dev_dist, int32_t* dev_dist2, void* stream);
 
 /* Copy one pyramid level of the last detect into a dense float32 device array
  * dev_dst of dims[octave] voxels (x fastest).  kind = SIFT3D_LEVEL_*.

@@ -176,6 +176,27 @@ def C_cast(ptr):
     return ctypes.cast(ptr, ctypes.POINTER(ctypes.c_uint8))
 
 
+def match(desc_a, desc_b, kind: int, stream=None, second: bool = True):
+    """Nearest neighbour in desc_b of every descriptor of desc_a, on the GPU
+    (sift3d_match).  BRIEF: int64/uint64 CUDA tensors of words; RRIEF: uint8
+    CUDA tensors of shape (n, 64) (or flat n*64).  Returns int32 CUDA tensors
+    (nn, dist, dist2) with dist2 None when second is False."""
+    import torch
+    if kind == DESC_BRIEF:
+        na, nb = desc_a.numel(), desc_b.numel()
+    else:
+        na, nb = desc_a.numel() // 64, desc_b.numel() // 64
+    dev = desc_a.device
+    nn = torch.empty(max(na, 1), dtype=torch.int32, device=dev)
+    dist = torch.empty(max(na, 1), dtype=torch.int32, device=dev)
+    dist2 = torch.empty(max(na, 1), dtype=torch.int32, device=dev) if second else None
+    rc = capi.sift3d_match(desc_a.data_ptr(), na, desc_b.data_ptr() if nb > 0 else 0, nb, kind, nn.data_ptr(),
+                           dist.data_ptr(), dist2.data_ptr() if second else 0, _stream_handle(stream))
+    if rc != capi.OK:
+        raise capi.Sift3DError(rc, "sift3d_match")
+    return nn[:na], dist[:na], (dist2[:na] if second else None)
+
+
 def keypoints_to_numpy(buf, n: int) -> np.ndarray:
     """Copy the first n records of a device keypoint byte tensor to a structured array."""
     if n <= 0:

@@ -103,6 +103,8 @@ SIGNATURES = {
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_int)]),
     "sift3d_stage_timeline": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                         C.POINTER(C.c_int)]),
+    "sift3d_match": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p]),
 }
 
 
@@ -233,3 +235,10 @@ def sift3d_stage_timeline(ctx, max_n: int = 512):
         return rc, []
     k = min(n.value, max_n)
     return rc, [(float(b[i]), float(e[i])) for i in range(k)]
+
+
+def sift3d_match(dev_a: int, na: int, dev_b: int, nb: int, kind: int, dev_nn: int, dev_dist: int, dev_dist2: int,
+                 stream: int) -> int:
+    """Nearest-neighbour matching; pointers are device addresses (0 = NULL)."""
+    return _lib.sift3d_match(C.c_void_p(dev_a), na, C.c_void_p(dev_b), nb, kind, C.c_void_p(dev_nn),
+                             C.c_void_p(dev_dist), C.c_void_p(dev_dist2), C.c_void_p(stream))

@@ -572,6 +572,27 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
 }
 
+int sift3d_match(const void* dev_a, int na, const void* dev_b, int nb, int kind, int32_t* dev_nn,
+                 int32_t* dev_dist, int32_t* dev_dist2, void* stream) {
+    if (kind != SIFT3D_DESC_BRIEF && kind != SIFT3D_DESC_RRIEF) return SIFT3D_EINVAL;
+    if (na < 0 || nb < 0) return SIFT3D_EINVAL;
+    if (na == 0) return SIFT3D_OK;
+    const uintptr_t align = kind == SIFT3D_DESC_BRIEF ? 8 : 16;
+    if (!dev_a || !dev_nn || !dev_dist || (nb > 0 && !dev_b)) return SIFT3D_EINVAL;
+    if (((uintptr_t)dev_a % align) != 0 || (nb > 0 && ((uintptr_t)dev_b % align) != 0)) return SIFT3D_EINVAL;
+    MatchArgs a{};
+    a.a = dev_a;
+    a.b = dev_b;
+    a.na = na;
+    a.nb = nb;
+    a.nn = dev_nn;
+    a.dist = dev_dist;
+    a.dist2 = dev_dist2;
+    const LaunchSpec s = match_spec(kind, a);
+    std::string err;
+    return launch(s, &a, static_cast<cudaStream_t>(stream), &err);
+}
+
 int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index, float* dev_dst, void* stream) {
     if (!ctx) return SIFT3D_EINVAL;
     if (!ctx->last) return set_err(ctx, SIFT3D_EINVAL, "read_level needs a prior detect");

@@ -143,6 +143,16 @@ struct DescribeArgs {
     uint8_t* rrief;
 };
 
+// ---- nearest-neighbour matching ------------------------------------------------
+struct MatchArgs {
+    const void* a;             // na descriptors (uint64 BRIEF words or 64-byte RRIEF rows)
+    const void* b;             // nb descriptors of the same kind
+    int na, nb;
+    int32_t* nn;               // per query: index of the nearest in b (-1 if nb == 0)
+    int32_t* dist;             //            its distance (INT_MAX if nb == 0)
+    int32_t* dist2;            //            second-nearest distance (INT_MAX if none), or null
+};
+
 struct ReadLevelArgs {
     const void* src;
     int64_t py, pz;
@@ -198,6 +208,7 @@ LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
+LaunchSpec match_spec(int kind, const MatchArgs& a);
 LaunchSpec tail_spec(int storage, const TailArgs& a);
 int tail_cluster_size(int storage, const TailArgs& a);   // 16, 8, or 0 (cannot run)
 // Row pitch of the small-octave kernel's shared slabs (odd: conflict-free columns).

@@ -61,7 +61,7 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (!(p.trunc > 0.0) || !(p.trunc <= 10.0)) return fail(err, "trunc must be in (0, 10]");
     if (!(p.desc_blur_sigma >= 0.0) || !std::isfinite(p.desc_blur_sigma))
         return fail(err, "desc_blur_sigma must be finite and >= 0");
-    if (p.desc_method != 3) return fail(err, "only desc_method 3 is implemented");
+    if (p.desc_method < 1 || p.desc_method > 5) return fail(err, "desc_method must be 1..5");
     if (p.storage < SIFT3D_STORAGE_F32 || p.storage > SIFT3D_STORAGE_BF16) return fail(err, "bad storage");
     if (p.max_keypoints < 0 || p.max_keypoints > (1 << 20)) return fail(err, "max_keypoints must be in 0..2^20");
     if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
@@ -218,18 +218,65 @@ struct SplitMix64 {
 };
 }  // namespace
 
+namespace {
+// mean + N(0, I), redrawn until every |coordinate| <= clip
+void normal_point(SplitMix64& g, const double* mean, double clip, double* q) {
+    for (;;) {
+        for (int c = 0; c < 3; ++c) q[c] = mean[c] + g.normal();
+        if (std::fabs(q[0]) <= clip && std::fabs(q[1]) <= clip && std::fabs(q[2]) <= clip) return;
+    }
+}
+
+// uniform in the ball of radius r: three uniforms on (-r, r), redrawn until inside
+void ball_point(SplitMix64& g, double r, double* q) {
+    for (;;) {
+        for (int c = 0; c < 3; ++c) q[c] = r * (2.0 * g.uniform() - 1.0);
+        if (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] <= r * r) return;
+    }
+}
+}  // namespace
+
+// Point pairs in units of the keypoint scale (Sec. 2.2.3):
+//   1: p1, p2 uniform in the ball of radius 2;   2: p1, p2 ~ N(0, I);
+//   3: p1 ~ N(0, I), p2 ~ N(p1, I);                4: p1 = 0, p2 ~ N(0, I);
+//   5: p1 = 0, p2 on the spherical grid radius {0.5, 1, 1.5, 2} x cos(theta)
+//      {0.75, 0.25, -0.25, -0.75} x azimuth pi/2 * a (+ pi/4 on odd rings),
+//      pair 16 m + 4 j + a.
+// Normal draws are redrawn while any |coordinate| > 4.
 void make_pattern(const sift3d_params& p, float* out) {
     SplitMix64 g{p.pattern_seed};
     const double clip = 4.0;
+    const double zero[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < SIFT3D_N_PAIRS; ++k) {
-        double p1[3], p2[3];
-        for (;;) {
-            for (int c = 0; c < 3; ++c) p1[c] = g.normal();
-            if (std::fabs(p1[0]) <= clip && std::fabs(p1[1]) <= clip && std::fabs(p1[2]) <= clip) break;
-        }
-        for (;;) {
-            for (int c = 0; c < 3; ++c) p2[c] = p1[c] + g.normal();
-            if (std::fabs(p2[0]) <= clip && std::fabs(p2[1]) <= clip && std::fabs(p2[2]) <= clip) break;
+        double p1[3] = {0.0, 0.0, 0.0}, p2[3] = {0.0, 0.0, 0.0};
+        switch (p.desc_method) {
+            case 1:
+                ball_point(g, 2.0, p1);
+                ball_point(g, 2.0, p2);
+                break;
+            case 2:
+                normal_point(g, zero, clip, p1);
+                normal_point(g, zero, clip, p2);
+                break;
+            case 4:
+                normal_point(g, zero, clip, p2);
+                break;
+            case 5: {
+                static const double radii[4] = {0.5, 1.0, 1.5, 2.0};
+                static const double cos_theta[4] = {0.75, 0.25, -0.25, -0.75};
+                const int m = (k / 16) % 4, j = (k / 4) % 4, a = k % 4;
+                const double pi = 3.14159265358979323846;
+                const double ct = cos_theta[j], st = std::sqrt(1.0 - ct * ct);
+                const double phi = 0.5 * pi * a + (j % 2 == 1 ? 0.25 * pi : 0.0);
+                p2[0] = radii[m] * st * std::cos(phi);
+                p2[1] = radii[m] * st * std::sin(phi);
+                p2[2] = radii[m] * ct;
+                break;
+            }
+            default:   // 3
+                normal_point(g, zero, clip, p1);
+                normal_point(g, p1, clip, p2);
+                break;
         }
         for (int c = 0; c < 3; ++c) {
             out[k * 6 + c] = (float)p1[c];

@@ -97,10 +97,11 @@ def test_algorithmic_byte_model(lib):
 
 
 @pytest.mark.parametrize("seed", [0x5EED5EED, 0, 1234567, 2 ** 63 + 11])
-def test_pattern_matches_oracle_generator(lib, seed):
+@pytest.mark.parametrize("method", [1, 2, 3, 4, 5])
+def test_pattern_matches_oracle_generator(lib, seed, method):
     from paper_2112_10258_gb300 import pattern
-    got = pattern(pattern_seed=seed)
-    ref = O.pattern_method3(seed)
+    got = pattern(pattern_seed=seed, desc_method=method)
+    ref = O.pattern_for(O.Params(desc_method=method, pattern_seed=seed))
     assert got.dtype == np.float32 and got.shape == (64, 2, 3)
     np.testing.assert_array_equal(got, ref.astype(np.float32))
 
@@ -108,7 +109,8 @@ def test_pattern_matches_oracle_generator(lib, seed):
 @pytest.mark.parametrize("field,value", [
     ("sigma0", 0.4), ("scales_per_octave", 0), ("scales_per_octave", 6), ("sign_sum_min", 0),
     ("sign_sum_min", 81), ("border", 0), ("min_octave_dim", 2), ("contrast_thresh", -1.0),
-    ("curvature_r", 0.5), ("trunc", 0.0), ("desc_method", 1), ("storage", 3), ("max_inflight", 0),
+    ("curvature_r", 0.5), ("trunc", 0.0), ("desc_method", 0), ("desc_method", 6), ("storage", 3),
+    ("max_inflight", 0),
     ("trunc", 10.0),   # radius ceil(10 * 3.09) > 16
 ])
 def test_invalid_params_rejected(lib, field, value):
@@ -148,3 +150,12 @@ def test_plan_for_volume_below_min_octave_dim(lib):
     from paper_2112_10258_gb300 import plan
     pl = plan(15, 80, 80)
     assert pl["n_octaves"] == 0 and pl["algorithmic_bytes"] == 0
+
+
+def test_match_rejects_bad_arguments_without_device(lib):
+    from paper_2112_10258_gb300 import capi
+    assert capi.sift3d_match(0, 0, 0, 0, 1, 0, 0, 0, 0) == capi.OK          # na == 0: nothing to do
+    assert capi.sift3d_match(0, 4, 0, 4, 3, 0, 0, 0, 0) == capi.EINVAL      # kind
+    assert capi.sift3d_match(0, -1, 0, 4, 1, 0, 0, 0, 0) == capi.EINVAL     # negative count
+    assert capi.sift3d_match(0, 4, 0, 4, 1, 0, 0, 0, 0) == capi.EINVAL      # NULL pointers
+    assert capi.sift3d_match(8, 4, 8, 4, 2, 16, 16, 0, 0) == capi.EINVAL    # RRIEF rows not 16-byte aligned

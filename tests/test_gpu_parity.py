@@ -103,6 +103,22 @@ def test_blob_case_64cubed_keypoints_and_descriptors(S):
     det.close()
 
 
+@pytest.mark.parametrize("method", [1, 2, 4, 5])
+def test_descriptor_point_selection_methods(S, method):
+    """Sec. 2.2.3 point-selection methods 1, 2, 4 and 5 (method 3 is the default
+    every other test uses): BRIEF bits and RRIEF ranks equal the oracle's for the
+    same pattern, up to flagged near ties."""
+    vol = blob_volume(seed=3, shape=(48, 44, 40), n_blobs=20)
+    det, buf, n, kps = _run(S, vol, desc_method=method)
+    p = _oracle_params(desc_method=method)
+    ref = O.detect(vol, p)
+    compare_keypoints(kps, ref)
+    assert n > 0
+    dexc = _check_descriptors(S, det, buf, n, kps, ref, p)
+    assert dexc <= max(2, n // 10)
+    det.close()
+
+
 @pytest.fixture(scope="module")
 def brain():
     vol = brain_like_volume(seed=0)
