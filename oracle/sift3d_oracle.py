@@ -650,3 +650,69 @@ def match(desc_a: np.ndarray, desc_b: np.ndarray, kind: int):
     squared rank distance).  Returns nearest_neighbours of the distance matrix."""
     d = hamming_distances(desc_a, desc_b) if kind == 1 else rank_distances(desc_a, desc_b)
     return nearest_neighbours(d)
+
+
+# ----------------------------------------------------------------------------------
+# Sub-voxel refinement (no counterpart in the paper: the quadratic interpolation
+# of Brown & Lowe, written for the 4D (x, y, z, scale) DoG stack)
+# ----------------------------------------------------------------------------------
+
+_REFINE_AXES = ((0, 0, 0, 1), (0, 0, 1, 0), (0, 1, 0, 0), (1, 0, 0, 0))   # x, y, z, level as (dl, dz, dy, dx)
+
+
+def refine_derivatives(D: list, s: int, iz: int, iy: int, ix: int):
+    """Centre value c, gradient g and Hessian H of the DoG stack at (ix, iy, iz)
+    of level s, by central differences with unit steps in x, y, z and the level
+    index (the usual 3-point first and second differences, and the 4-point
+    mixed differences)."""
+    def v(d):
+        dl, dz, dy, dx = d
+        return float(D[s + dl][iz + dz, iy + dy, ix + dx])
+
+    def add(a, b, sa=1, sb=1):
+        return tuple(sa * x + sb * y for x, y in zip(a, b))
+
+    zero = (0, 0, 0, 0)
+    c = v(zero)
+    g = np.zeros(4)
+    H = np.zeros((4, 4))
+    for a, ea in enumerate(_REFINE_AXES):
+        g[a] = 0.5 * (v(ea) - v(add(zero, ea, 1, -1)))
+        H[a, a] = v(ea) + v(add(zero, ea, 1, -1)) - 2.0 * c
+        for b in range(a + 1, 4):
+            eb = _REFINE_AXES[b]
+            H[a, b] = H[b, a] = 0.25 * (v(add(ea, eb)) - v(add(ea, eb, 1, -1)) - v(add(ea, eb, -1, 1))
+                                        + v(add(ea, eb, -1, -1)))
+    return c, g, H
+
+
+def refine_offset(D: list, s: int, iz: int, iy: int, ix: int):
+    """One Newton step on the 4D quadratic through the samples: offset =
+    -H^-1 g in (x, y, z, level) units and the interpolated value
+    c + g.offset / 2.  Returns (offset (4,), value, ok, cond(H)); ok is False
+    (offset 0, value c) when H is singular to working precision."""
+    c, g, H = refine_derivatives(D, s, iz, iy, ix)
+    cond = float(np.linalg.cond(H)) if np.all(np.isfinite(H)) else np.inf
+    if not cond < 1e12:
+        return np.zeros(4), c, False, cond
+    off = -np.linalg.solve(H, g)
+    return off, c + 0.5 * float(g @ off), True, cond
+
+
+def refine_keypoints(pyr: Pyramid, kps: np.ndarray, p: Params):
+    """Refined (x, y, z, sigma) in input voxels and the interpolated DoG value of
+    each keypoint: position ((i + offset) + 0.5) 2^o - 0.5 per axis, sigma
+    sigma0 2^((s + offset_s) / S) 2^o.  Returns (offsets (n, 4), values (n,),
+    coords (n, 4), ok (n,), cond (n,))."""
+    S = p.scales_per_octave
+    n = kps.size
+    offs, vals, coords = np.zeros((n, 4)), np.zeros(n), np.zeros((n, 4))
+    ok, cond = np.zeros(n, bool), np.zeros(n)
+    for i in range(n):
+        o, s = int(kps["octave"][i]), int(kps["scale"][i])
+        ix, iy, iz = int(kps["ix"][i]), int(kps["iy"][i]), int(kps["iz"][i])
+        offs[i], vals[i], ok[i], cond[i] = refine_offset(pyr.D[o], s, iz, iy, ix)
+        scale = float(1 << o)
+        coords[i, :3] = (np.array([ix, iy, iz], float) + offs[i, :3] + 0.5) * scale - 0.5
+        coords[i, 3] = p.sigma0 * 2.0 ** ((s + offs[i, 3]) / S) * scale
+    return offs, vals, coords, ok, cond

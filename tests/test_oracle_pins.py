@@ -551,3 +551,40 @@ def test_nearest_neighbours_ties_and_edges():
     W = rng.integers(0, 2 ** 63, 20, dtype=np.uint64)
     nn, d1, _ = O.match(W, W, 1)
     assert nn.tolist() == list(range(20)) and not d1.any()
+
+
+# ------------------------------------------------------------------ sub-voxel refinement
+
+
+def _quadratic_stack(centre, H, g0, c0, shape=(7, 7, 7), levels=5):
+    """D_l(z, y, x) = c0 + g0.u + u.H.u / 2 with u = (x, y, z, l) - centre."""
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    out = []
+    for l in range(levels):
+        u = np.stack([x - centre[0], y - centre[1], z - centre[2], np.full_like(x, l - centre[3])], axis=-1)
+        out.append(c0 + u @ g0 + 0.5 * np.einsum("...i,ij,...j->...", u, H, u))
+    return out
+
+
+def test_refinement_recovers_the_extremum_of_a_quadratic():
+    # central differences are exact for a quadratic, so one Newton step lands
+    # on its extremum: offset = true extremum - sample point
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(4, 4))
+    H = -(A @ A.T + 4 * np.eye(4))                  # negative definite: a maximum
+    ext = np.array([3.3, 2.8, 3.1, 2.2])             # extremum in (x, y, z, level)
+    D = _quadratic_stack(ext, H, np.zeros(4), 0.7)
+    off, val, ok, cond = O.refine_offset(D, 2, 3, 3, 3)
+    assert ok
+    np.testing.assert_allclose(off, ext - np.array([3, 3, 3, 2]), atol=1e-9)
+    assert abs(val - 0.7) < 1e-9                     # the value at the extremum
+
+
+def test_refinement_of_an_exact_sample_point_is_zero_and_singular_is_flagged():
+    H = -np.diag([1.0, 2.0, 3.0, 0.5])
+    D = _quadratic_stack(np.array([3.0, 3.0, 3.0, 2.0]), H, np.zeros(4), -0.2)
+    off, val, ok, _ = O.refine_offset(D, 2, 3, 3, 3)
+    assert ok and np.allclose(off, 0.0) and abs(val + 0.2) < 1e-12
+    flat = [np.zeros((7, 7, 7)) for _ in range(5)]
+    off, val, ok, cond = O.refine_offset(flat, 2, 3, 3, 3)
+    assert not ok and not off.any()
