@@ -127,6 +127,13 @@ typedef struct sift3d_params {
                                     thread-block cluster build their pyramids
                                     in one cluster launch (bitwise the same
                                     results; measured slower on GB300)       */
+    int32_t  refine;             /* 0 (default); 1 = one Newton step on the
+                                    4D (x, y, z, scale) quadratic of the DoG
+                                    through the keypoint's 3^4 neighbourhood
+                                    (central differences): x, y, z, sigma and
+                                    dog report the interpolated extremum.  No
+                                    counterpart in the paper; the keypoint set
+                                    does not change.                          */
     int32_t  use_pdl;            /* 0 (default); 1 = chain the detect graph's
                                     kernels with programmatic dependent launch;
                                     2 = only between kernels of octaves >= 1 */
@@ -141,8 +148,11 @@ typedef struct sift3d_keypoint {
     int32_t ix, iy, iz;          /* position in the octave grid                */
     int16_t octave, scale;       /* scale s in 1..S                            */
     int8_t  polarity;            /* +1 DoG peak, -1 valley                     */
-    int8_t  reserved0[3];
-    float   dog;                 /* D_s(ix,iy,iz)                              */
+    int8_t  refined;             /* 0 = refinement off; 1 = x, y, z, sigma, dog
+                                    refined (params.refine); 2 = its 4D
+                                    Hessian was singular: left at the voxel  */
+    int8_t  reserved0[2];
+    float   dog;                 /* D_s(ix,iy,iz), or the refined value        */
     int32_t sign_sum;            /* sum of signs over the 80 neighbours        */
     int32_t reserved1;
 } sift3d_keypoint;

@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("desc_method", C.c_int32),
         ("pattern_seed", C.c_uint64), ("storage", C.c_int32), ("use_graphs", C.c_int32),
         ("hbm_budget_bytes", C.c_uint64), ("max_keypoints", C.c_int32), ("max_inflight", C.c_int32),
-        ("fuse_small_octaves", C.c_int32), ("use_pdl", C.c_int32),
+        ("fuse_small_octaves", C.c_int32), ("refine", C.c_int32), ("use_pdl", C.c_int32),
     ]
 
 
@@ -56,7 +56,8 @@ class Keypoint(C.Structure):
     _fields_ = [
         ("x", C.c_float), ("y", C.c_float), ("z", C.c_float), ("sigma", C.c_float),
         ("ix", C.c_int32), ("iy", C.c_int32), ("iz", C.c_int32), ("octave", C.c_int16),
-        ("scale", C.c_int16), ("polarity", C.c_int8), ("reserved0", C.c_int8 * 3), ("dog", C.c_float),
+        ("scale", C.c_int16), ("polarity", C.c_int8), ("refined", C.c_int8), ("reserved0", C.c_int8 * 2),
+        ("dog", C.c_float),
         ("sign_sum", C.c_int32), ("reserved1", C.c_int32),
     ]
 
@@ -72,7 +73,7 @@ class Result(C.Structure):
 
 KEYPOINT_DTYPE = np.dtype([
     ("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("sigma", "<f4"), ("ix", "<i4"), ("iy", "<i4"),
-    ("iz", "<i4"), ("octave", "<i2"), ("scale", "<i2"), ("polarity", "i1"), ("reserved0", "i1", (3,)),
+    ("iz", "<i4"), ("octave", "<i2"), ("scale", "<i2"), ("polarity", "i1"), ("refined", "i1"), ("reserved0", "i1", (2,)),
     ("dog", "<f4"), ("sign_sum", "<i4"), ("reserved1", "<i4"),
 ])
 assert KEYPOINT_DTYPE.itemsize == C.sizeof(Keypoint) == 48

@@ -443,6 +443,7 @@ int sift3d_default_params(sift3d_params* out) {
     out->max_inflight = 4;
     out->fuse_small_octaves = 0;
     out->use_pdl = 0;
+    out->refine = 0;
     return SIFT3D_OK;
 }
 

@@ -93,6 +93,7 @@ struct PeakArgs {
     int octave, n_scales, border, sign_sum_min;
     float contrast, curv_k1, curv_k2;   // (2r+1)^3 and r^2
     float sigma_level[kMaxLevels];      // sigma_s in octave voxels
+    int refine;                         // report the 4D quadratic's extremum
     sift3d_keypoint* out;               // staging records
     int* count;                         // running total (all octaves)
     int capacity;

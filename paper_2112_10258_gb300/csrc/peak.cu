@@ -158,21 +158,86 @@ __device__ __forceinline__ bool full_test(const S* p, float c, int cut, float k1
     return A > 0.f && m2 > 0.f && det > 0.f && g > 0.f;
 }
 
+// Sub-voxel refinement (no counterpart in the paper): one Newton step on the 4D
+// quadratic through the staged 3^4 neighbourhood of centre p.  Gradient and
+// Hessian by central differences with unit steps in x, y, z and the level
+// index; the 4x4 system H off = -g is solved by Gaussian elimination with
+// partial pivoting in float32.  Returns 1 (off[4], *val = c + g.off / 2) or 2
+// when a pivot vanishes against the Hessian's largest entry (off = 0, *val = c).
+template <typename S>
+__device__ __noinline__ int refine_point(const S* p, float c, float* off, float* val) {
+    constexpr int BX = box_w<S>();
+    const int step[4] = {1, BX, SY * BX, SZ * SY * BX};   // x, y, z, level
+    float M[4][5];
+    float hmax = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float vp = ld(p + step[a]), vm = ld(p - step[a]);
+        M[a][4] = -0.5f * (vp - vm);                       // -g
+        M[a][a] = vp + vm - 2.0f * c;
+        hmax = fmaxf(hmax, fabsf(M[a][a]));
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+            const float h = 0.25f * (ld(p + step[a] + step[b]) - ld(p + step[a] - step[b]) -
+                                     ld(p - step[a] + step[b]) + ld(p - step[a] - step[b]));
+            M[a][b] = M[b][a] = h;
+            hmax = fmaxf(hmax, fabsf(h));
+        }
+    }
+    float g[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) g[a] = -M[a][4];
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (fabsf(M[r][col]) > fabsf(M[piv][col])) piv = r;
+        if (!(fabsf(M[piv][col]) > 1e-6f * hmax)) {
+            off[0] = off[1] = off[2] = off[3] = 0.f;
+            *val = c;
+            return 2;
+        }
+        if (piv != col)
+            for (int k = 0; k < 5; ++k) {
+                const float t = M[col][k];
+                M[col][k] = M[piv][k];
+                M[piv][k] = t;
+            }
+        for (int r = col + 1; r < 4; ++r) {
+            const float f = M[r][col] / M[col][col];
+            for (int k = col; k < 5; ++k) M[r][k] -= f * M[col][k];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        float acc = M[r][4];
+        for (int k = r + 1; k < 4; ++k) acc -= M[r][k] * off[k];
+        off[r] = acc / M[r][r];
+    }
+    *val = c + 0.5f * (g[0] * off[0] + g[1] * off[1] + g[2] * off[2] + g[3] * off[3]);
+    return 1;
+}
+
+// Writes keypoint record `slot`; p is the staged centre (for the refinement).
+template <typename S>
 __device__ __forceinline__ void write_keypoint(const PeakArgs& a, int slot, int x, int y, int z, int s, int ssum,
-                                               float c, float scale) {
+                                               float c, float scale, const S* p) {
     sift3d_keypoint k;
-    k.x = ((float)x + 0.5f) * scale - 0.5f;
-    k.y = ((float)y + 0.5f) * scale - 0.5f;
-    k.z = ((float)z + 0.5f) * scale - 0.5f;
-    k.sigma = a.sigma_level[s] * scale;
+    float off[4] = {0.f, 0.f, 0.f, 0.f};
+    float val = c;
+    int refined = 0;
+    if (a.refine) refined = refine_point<S>(p, c, off, &val);
+    k.x = ((float)x + off[0] + 0.5f) * scale - 0.5f;
+    k.y = ((float)y + off[1] + 0.5f) * scale - 0.5f;
+    k.z = ((float)z + off[2] + 0.5f) * scale - 0.5f;
+    k.sigma = a.sigma_level[s] * (refined == 1 ? exp2f(off[3] / (float)a.n_scales) : 1.0f) * scale;
     k.ix = x;
     k.iy = y;
     k.iz = z;
     k.octave = (int16_t)a.octave;
     k.scale = (int16_t)s;
     k.polarity = ssum > 0 ? 1 : -1;
-    k.reserved0[0] = k.reserved0[1] = k.reserved0[2] = 0;
-    k.dog = c;
+    k.refined = (int8_t)refined;
+    k.reserved0[0] = k.reserved0[1] = 0;
+    k.dog = val;
     k.sign_sum = ssum;
     k.reserved1 = 0;
     a.out[slot] = k;
@@ -186,7 +251,7 @@ __device__ __noinline__ void test_overflow(const PeakArgs& a, const S* p, float 
     int ssum = 0;
     if (full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum)) {
         const int slot = atomicAdd(a.count, 1);
-        if (slot < a.capacity) write_keypoint(a, slot, x, y, z, s, ssum, c, scale);
+        if (slot < a.capacity) write_keypoint<S>(a, slot, x, y, z, s, ssum, c, scale, p);
     }
 }
 
@@ -276,14 +341,15 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
         bool kp = false;
         int ssum = 0, kx = 0, ky = 0, kz = 0, s = 1;
         float c = 0.f;
+        const S* pc = sm;
         if (i < n) {
             const unsigned e = surv[i];
             const int l = e & 31, ww = (e >> 5) & 7, tz = (e >> 8) & 7;
             s = (e >> 12) & 7;
             kx = xs + 1 + l, ky = ys + 1 + ww, kz = zs + 1 + tz;
-            const S* p = sm + s * LV + (tz + 1) * PL + (ww + 1) * BX + l + 1;
-            c = ld(p);
-            kp = full_test<S>(p, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum);
+            pc = sm + s * LV + (tz + 1) * PL + (ww + 1) * BX + l + 1;
+            c = ld(pc);
+            kp = full_test<S>(pc, c, a.sign_sum_min, a.curv_k1, a.curv_k2, &ssum);
         }
         const unsigned m = __ballot_sync(0xffffffffu, kp);
         if (m == 0u) continue;
@@ -293,7 +359,7 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
         slot0 = __shfl_sync(0xffffffffu, slot0, leader);
         if (!kp) continue;
         const int slot = slot0 + __popc(m & ((1u << lane) - 1u));
-        if (slot < a.capacity) write_keypoint(a, slot, kx, ky, kz, s, ssum, c, scale);
+        if (slot < a.capacity) write_keypoint<S>(a, slot, kx, ky, kz, s, ssum, c, scale, pc);
     }
 }
 

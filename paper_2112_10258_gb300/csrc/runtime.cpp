@@ -66,6 +66,7 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.max_keypoints < 0 || p.max_keypoints > (1 << 20)) return fail(err, "max_keypoints must be in 0..2^20");
     if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
     if (p.use_pdl < 0 || p.use_pdl > 2) return fail(err, "use_pdl must be 0, 1 or 2");
+    if (p.refine < 0 || p.refine > 1) return fail(err, "refine must be 0 or 1");
     if (p.fuse_small_octaves < 0 || p.fuse_small_octaves > 1) return fail(err, "fuse_small_octaves must be 0 or 1");
 
     // filter radii of the schedule
@@ -402,6 +403,7 @@ PeakArgs make_peak_args(const Workspace& ws, int o) {
     pa.curv_k1 = (float)((2.0 * r + 1.0) * (2.0 * r + 1.0) * (2.0 * r + 1.0));
     pa.curv_k2 = (float)(r * r);
     for (int s = 0; s < pl.L; ++s) pa.sigma_level[s] = (float)pl.sig_level[s];
+    pa.refine = pl.p.refine;
     pa.out = ws.staging;
     pa.count = ws.count;
     pa.capacity = ws.capacity;
