@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="direct launches instead of the CUDA graph")
     ap.add_argument("--inflight", type=int, default=1,
                     help="volumes processed concurrently (separate contexts/streams, distinct inputs)")
-    ap.add_argument("--mode", choices=["headline", "batched", "serving"], default="headline",
-                    help="batched: many uneven volumes per step; serving: Poisson request stream")
+    ap.add_argument("--mode", choices=["headline", "batched", "serving", "match"], default="headline",
+                    help="batched: many uneven volumes per step; serving: Poisson request stream; "
+                         "match: nearest-neighbour matching of descriptor sets")
+    ap.add_argument("--match-n", type=int, default=3000, help="descriptors per set in --mode match")
     ap.add_argument("--batch-n", type=int, default=256, help="volumes per batched step")
     ap.add_argument("--requests", type=int, default=600, help="requests in the serving run")
     ap.add_argument("--rate", type=float, default=200.0, help="serving arrival rate (volumes/s)")
@@ -390,6 +392,42 @@ def run_serving(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- matching mode
+def run_match(args, rank, world, local):
+    """Nearest-neighbour matching (sift3d_match) of two sets of --match-n
+    descriptors (the paper's volumes hold about 3000 keypoints), BRIEF and
+    RRIEF, device resident; CUDA events over K calls each."""
+    import torch
+    import paper_2112_10258_gb300 as S
+    n = args.match_n
+    g = torch.Generator(device="cpu").manual_seed(1234 + rank)
+    ba = torch.randint(-2 ** 62, 2 ** 62, (n,), generator=g, dtype=torch.int64).cuda()
+    bb = torch.randint(-2 ** 62, 2 ** 62, (n,), generator=g, dtype=torch.int64).cuda()
+    ra = torch.stack([torch.randperm(64, generator=g) for _ in range(n)]).to(torch.uint8).cuda()
+    rb = torch.stack([torch.randperm(64, generator=g) for _ in range(n)]).to(torch.uint8).cuda()
+    out = {}
+    for name, kind, a, b in (("brief", S.DESC_BRIEF, ba, bb), ("rrief", S.DESC_RRIEF, ra, rb)):
+        for _ in range(args.warmup):
+            S.match(a, b, kind)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            S.match(a, b, kind)
+        e1.record()
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / args.steps
+        out[name] = {"us_per_match": us, "pairs_per_s": n * n / (us * 1e-6)}
+    if rank == 0:
+        print(json.dumps({"mode": "match", "metric": f"nearest-neighbour matching of {n} x {n} descriptors",
+                          "value": out["rrief"]["us_per_match"], "unit": "us (RRIEF)", "higher_is_better": False,
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "brief": out["brief"],
+                          "rrief": out["rrief"], "data": "synthetic (random words / rank permutations)",
+                          "config": {"workload": f"{n} query descriptors against {n}, best + second best"}}),
+              flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -412,6 +450,9 @@ def main():
         return
     if args.mode == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.mode == "match":
+        run_match(args, rank, world, local)
         return
     dist = None
     if world > 1:
