@@ -716,3 +716,133 @@ def refine_keypoints(pyr: Pyramid, kps: np.ndarray, p: Params):
         coords[i, :3] = (np.array([ix, iy, iz], float) + offs[i, :3] + 0.5) * scale - 0.5
         coords[i, 3] = p.sigma0 * 2.0 ** ((s + offs[i, 3]) / S) * scale
     return offs, vals, coords, ok, cond
+
+
+# ----------------------------------------------------------------------------------
+# 3D SIFT-Rank descriptor (the paper's comparison baseline, Sec. 1 and Sec. 3.5:
+# dominant orientation from peaks of a discrete spherical histogram of gradient,
+# a 3x3 rotation; 2x2x2 spatial x 8 orientation bins = 64 elements after
+# reorientation; rank normalisation).  The paper gives no further detail; the
+# sampling grid, the 12-direction histogram and the octant binning below are
+# this implementation's reading.
+# ----------------------------------------------------------------------------------
+
+SR_GRID = 8            # samples per axis of the cube [-r, r]^3, r = SR_RADIUS * sigma
+SR_RADIUS = 3.0
+
+
+def icosahedron_directions() -> np.ndarray:
+    """The 12 unit vertices of the regular icosahedron: cyclic permutations of
+    (0, +-1, +-phi), normalised; order: (0, a, b), (a, b, 0), (b, 0, a) with
+    a, b running over +-1, +-phi."""
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    out = []
+    for a in (1.0, -1.0):
+        for b in (phi, -phi):
+            out.append((0.0, a, b))
+    for a in (1.0, -1.0):
+        for b in (phi, -phi):
+            out.append((a, b, 0.0))
+    for a in (1.0, -1.0):
+        for b in (phi, -phi):
+            out.append((b, 0.0, a))
+    v = np.array(out)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def siftrank_samples(sigma: float):
+    """Sample offsets u (n, 3) and Gaussian weights w (n,): the SR_GRID^3 cell
+    centres of [-r, r]^3, r = 3 sigma, that lie in the ball |u| <= r, weighted
+    by exp(-|u|^2 / (2 (r/2)^2))."""
+    r = SR_RADIUS * sigma
+    t = ((np.arange(SR_GRID) + 0.5) / SR_GRID * 2.0 - 1.0) * r
+    z, y, x = np.meshgrid(t, t, t, indexing="ij")
+    u = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    keep = np.sum(u * u, axis=1) <= r * r
+    u = u[keep]
+    w = np.exp(-np.sum(u * u, axis=1) / (2.0 * (0.5 * r) ** 2))
+    return u, w
+
+
+def siftrank_gradients(G: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Gradient of G at points (n, 3) (x, y, z) by central differences of
+    trilinear samples (coordinates clamped to the grid), unit steps."""
+    g = np.zeros_like(pts)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = 1.0
+        vp, _ = trilinear_clamp(G, pts + e)
+        vm, _ = trilinear_clamp(G, pts - e)
+        g[:, a] = 0.5 * (vp - vm)
+    return g
+
+
+def siftrank_orientation(g: np.ndarray, w: np.ndarray):
+    """Rotation R = [e1 e2 e3] (columns) from the gradients: e1 is the weighted
+    mean gradient of the peak bin of the 12-direction histogram (each gradient
+    votes w |g| into its nearest icosahedron direction); e2 is the same for the
+    components perpendicular to e1, made exactly perpendicular; e3 = e1 x e2.
+    Returns (R, margin): margin is the smallest of the relative gaps between
+    each histogram's peak bin and its runner-up, and of the gaps between each
+    vector's nearest and second-nearest direction (near-tie bookkeeping)."""
+    V = icosahedron_directions()
+
+    def peak(vec):
+        mag = np.linalg.norm(vec, axis=1)
+        dots = vec @ V.T
+        b = np.argmax(dots, axis=1)
+        srt = np.sort(dots, axis=1)
+        vgap = float(np.min((srt[:, -1] - srt[:, -2]) / np.maximum(mag, 1e-300)))   # nearest-vertex margin
+        hist = np.zeros(12)
+        np.add.at(hist, b, w * mag)
+        m = int(np.argmax(hist))
+        top = np.sort(hist)[::-1]
+        gap = (top[0] - top[1]) / max(top[0], 1e-300)
+        mean = (w[b == m, None] * vec[b == m]).sum(axis=0)
+        return mean, min(gap, vgap)
+
+    m1, gap1 = peak(g)
+    e1 = m1 / np.linalg.norm(m1)
+    gp = g - np.outer(g @ e1, e1)
+    m2, gap2 = peak(gp)
+    m2 = m2 - (m2 @ e1) * e1
+    e2 = m2 / np.linalg.norm(m2)
+    e3 = np.cross(e1, e2)
+    return np.stack([e1, e2, e3], axis=1), min(gap1, gap2)
+
+
+def siftrank_descriptor(G: np.ndarray, c: np.ndarray, sigma: float):
+    """64 rank-normalised gradient histogram of the keypoint at c (octave voxels)
+    with scale sigma (octave voxels).  Samples at c + R u, gradients rotated into
+    the keypoint frame (g' = R^T g); spatial bin = octant of u (x fastest),
+    orientation bin = octant of g'; element 8 * spatial + orientation gets
+    w |g'|.  Returns (ranks (64,), histogram (64,), R, decision margin)."""
+    u, w = siftrank_samples(sigma)
+    g0 = siftrank_gradients(G, c + u)
+    R, gap = siftrank_orientation(g0, w)
+    pts = c + u @ R.T
+    g = siftrank_gradients(G, pts) @ R                  # g' = R^T g, row-wise
+    sb = (u[:, 0] >= 0) + 2 * (u[:, 1] >= 0) + 4 * (u[:, 2] >= 0)
+    ob = (g[:, 0] >= 0) + 2 * (g[:, 1] >= 0) + 4 * (g[:, 2] >= 0)
+    hist = np.zeros(64)
+    np.add.at(hist, 8 * sb + ob, w * np.linalg.norm(g, axis=1))
+    nrm = np.linalg.norm(g, axis=1)
+    edge = min(float(np.min(np.abs(g) / np.maximum(nrm[:, None], 1e-300))), gap)
+    return rank_order(hist[None])[0].astype(np.uint8), hist, R, edge
+
+
+def siftrank(pyr: Pyramid, kps: np.ndarray, p: Params):
+    """SIFT-Rank descriptors of keypoints on their Gaussian level G_s (not
+    pre-blurred).  Returns (ranks (n, 64) uint8, hists (n, 64), R (n, 3, 3),
+    margins (n,))."""
+    sig = level_sigmas(p)
+    n = kps.size
+    ranks = np.zeros((n, 64), np.uint8)
+    hists = np.zeros((n, 64))
+    rots = np.zeros((n, 3, 3))
+    margins = np.zeros(n)
+    for i in range(n):
+        o, s = int(kps["octave"][i]), int(kps["scale"][i])
+        c = np.array([kps["ix"][i], kps["iy"][i], kps["iz"][i]], np.float64)
+        ranks[i], hists[i], rots[i], margins[i] = siftrank_descriptor(pyr.G[o][s], c, sig[s])
+    return ranks, hists, rots, margins

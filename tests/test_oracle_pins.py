@@ -588,3 +588,49 @@ def test_refinement_of_an_exact_sample_point_is_zero_and_singular_is_flagged():
     flat = [np.zeros((7, 7, 7)) for _ in range(5)]
     off, val, ok, cond = O.refine_offset(flat, 2, 3, 3, 3)
     assert not ok and not off.any()
+
+
+# ------------------------------------------------------------------ 3D SIFT-Rank
+
+
+def test_icosahedron_directions():
+    V = O.icosahedron_directions()
+    np.testing.assert_allclose(np.linalg.norm(V, axis=1), 1.0, atol=1e-15)
+    D = V @ V.T
+    off = D[~np.eye(12, dtype=bool)]
+    # every other vertex is at dot +-1/sqrt(5), except the antipode at -1
+    assert np.all((np.abs(np.abs(off) - 1 / np.sqrt(5)) < 1e-12) | (np.abs(off + 1) < 1e-12))
+    assert np.all(np.sum(np.abs(D - 1 / np.sqrt(5)) < 1e-12, axis=1) == 5)   # five nearest neighbours each
+
+
+def _analytic_volume(fn, shape=(40, 40, 40)):
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    return fn(x, y, z)
+
+
+def test_siftrank_orientation_follows_the_dominant_gradient():
+    G = _analytic_volume(lambda x, y, z: 2.0 * x + 0.5 * np.sin(0.7 * y) + 0.05 * np.cos(0.3 * z))
+    ranks, hist, R, margin = O.siftrank_descriptor(G, np.array([20.0, 20.0, 20.0]), 2.0)
+    assert abs(R[:, 0] @ [1, 0, 0]) > 0.99                  # e1 along the dominant x gradient
+    assert abs(R[:, 1] @ [0, 1, 0]) > 0.95                  # e2 along the next (y) structure
+    np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-12)
+    assert np.linalg.det(R) > 0
+    assert sorted(ranks.tolist()) == list(range(64))
+
+
+def test_siftrank_invariances():
+    G = _analytic_volume(lambda x, y, z: np.sin(0.3 * x + 0.1 * y) * np.cos(0.25 * z - 0.2 * y) + 0.1 * x)
+    c = np.array([19.0, 21.0, 18.0])
+    r0, h0, R0, _ = O.siftrank_descriptor(G, c, 2.2)
+    r1, h1, R1, _ = O.siftrank_descriptor(3.0 * G + 7.0, c, 2.2)           # affine intensity
+    np.testing.assert_array_equal(r0, r1)
+    np.testing.assert_allclose(R0, R1, atol=1e-9)
+    Gs = np.roll(G, (2, -3, 4), axis=(0, 1, 2))                               # integer translation
+    r2, _, R2, _ = O.siftrank_descriptor(Gs, c + np.array([4.0, -3.0, 2.0]), 2.2)
+    np.testing.assert_array_equal(r0, r2)
+    # I -> -I: e1, e2 flip and e3 stays, so the spatial x, y bits and the
+    # orientation z bit of every element flip: a fixed permutation of the bins
+    r3, h3, R3, _ = O.siftrank_descriptor(-G, c, 2.2)
+    np.testing.assert_allclose(R3, R0 * np.array([-1.0, -1.0, 1.0]), atol=1e-9)
+    perm = np.array([8 * ((k // 8) ^ 3) + ((k % 8) ^ 4) for k in range(64)])
+    np.testing.assert_allclose(h3[perm], h0, rtol=1e-9)
