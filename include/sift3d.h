@@ -300,6 +300,28 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
 int sift3d_gaussian_blur_noalloc(const float* dev_in, int nx, int ny, int nz, double sigma,
                                  double trunc, float* dev_out, void* stream);
 
+/* 3D SIFT-Rank descriptors of keypoints from the last detect on ctx: the
+ * paper's comparison baseline (Sec. 1 and Sec. 3.5), of which the paper fixes
+ * a dominant 3x3 orientation from peaks of a discrete spherical histogram of
+ * gradient, 2x2x2 spatial x 8 orientation bins after reorientation, and rank
+ * normalisation.  This library's reading of the rest: on the keypoint's
+ * level G_s (not pre-blurred), gradients by central differences of trilinear
+ * samples at the 8^3 cell centres of [-r, r]^3 inside the ball of radius
+ * r = 3 sigma_s (280 samples, weight exp(-|u|^2 / (2 (r/2)^2))); e1 = the
+ * weighted mean gradient of the peak bin of a histogram of w |g| over the 12
+ * icosahedron directions, e2 the same for the gradients' parts perpendicular
+ * to e1, e3 = e1 x e2; the samples are then taken at c + R u, and element
+ * 8 * octant(u) + octant(R^T g) (octant = (x >= 0) + 2 (y >= 0) + 4 (z >= 0))
+ * accumulates w |g|; the output is the rank of each of the 64 values,
+ * ascending, ties by lower index.
+ *   n         number of keypoints in dev_kps; -1 = the device-side count of
+ *             the last detect (no host wait).
+ *   dev_desc  n x 64 uint8 ranks (device, caller owned).
+ *   dev_rot   n x 9 floats, R row-major with columns e1, e2, e3, or NULL.
+ * Errors: SIFT3D_EINVAL (no prior detect, NULL outputs), SIFT3D_ECUDA. */
+int sift3d_describe_siftrank(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, uint8_t* dev_desc,
+                             float* dev_rot, void* stream);
+
 /* Nearest-neighbour matching of descriptors (Sec. 2.1 (e): descriptors are
  * matched by nearest neighbour).  For each descriptor i of set A the call
  * finds, by brute force over set B:

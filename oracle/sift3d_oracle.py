@@ -729,6 +729,7 @@ def refine_keypoints(pyr: Pyramid, kps: np.ndarray, p: Params):
 
 SR_GRID = 8            # samples per axis of the cube [-r, r]^3, r = SR_RADIUS * sigma
 SR_RADIUS = 3.0
+SR_NEGLIGIBLE = 1e-5   # votes below this fraction of the largest bin do not count in the margins
 
 
 def icosahedron_directions() -> np.ndarray:
@@ -791,10 +792,18 @@ def siftrank_orientation(g: np.ndarray, w: np.ndarray):
         mag = np.linalg.norm(vec, axis=1)
         dots = vec @ V.T
         b = np.argmax(dots, axis=1)
-        srt = np.sort(dots, axis=1)
-        vgap = float(np.min((srt[:, -1] - srt[:, -2]) / np.maximum(mag, 1e-300)))   # nearest-vertex margin
         hist = np.zeros(12)
         np.add.at(hist, b, w * mag)
+        # nearest-vertex margin of the samples whose vote is not negligible
+        # (a zero gradient, e.g. from clamped samples, votes nothing either way)
+        # Exact ties between two directions come from exactly zero gradient
+        # components (clamped samples at the border); they are decided the same
+        # way (lowest index) in any precision, so only non-zero gaps count.
+        big = w * mag > SR_NEGLIGIBLE * max(hist.max(), 1e-300)
+        srt = np.sort(dots[big], axis=1)
+        gaps = (srt[:, -1] - srt[:, -2]) / mag[big]
+        gaps = gaps[gaps > 0.0]
+        vgap = float(np.min(gaps)) if gaps.size else 1.0
         m = int(np.argmax(hist))
         top = np.sort(hist)[::-1]
         gap = (top[0] - top[1]) / max(top[0], 1e-300)
@@ -802,10 +811,15 @@ def siftrank_orientation(g: np.ndarray, w: np.ndarray):
         return mean, min(gap, vgap)
 
     m1, gap1 = peak(g)
+    if not np.linalg.norm(m1) > 0.0:                  # no gradient at all: the identity frame
+        return np.eye(3), 0.0
     e1 = m1 / np.linalg.norm(m1)
     gp = g - np.outer(g @ e1, e1)
     m2, gap2 = peak(gp)
     m2 = m2 - (m2 @ e1) * e1
+    if not np.linalg.norm(m2) > 0.0:                  # no perpendicular gradient: any perpendicular axis
+        m2 = np.cross(e1, [1.0, 0.0, 0.0] if abs(e1[0]) < 0.9 else [0.0, 1.0, 0.0])
+        gap2 = 0.0
     e2 = m2 / np.linalg.norm(m2)
     e3 = np.cross(e1, e2)
     return np.stack([e1, e2, e3], axis=1), min(gap1, gap2)
@@ -827,7 +841,8 @@ def siftrank_descriptor(G: np.ndarray, c: np.ndarray, sigma: float):
     hist = np.zeros(64)
     np.add.at(hist, 8 * sb + ob, w * np.linalg.norm(g, axis=1))
     nrm = np.linalg.norm(g, axis=1)
-    edge = min(float(np.min(np.abs(g) / np.maximum(nrm[:, None], 1e-300))), gap)
+    big = w * nrm > SR_NEGLIGIBLE * max(hist.max(), 1e-300)          # octant decisions that matter
+    edge = min(float(np.min(np.abs(g[big]) / nrm[big, None])) if big.any() else 1.0, gap)
     return rank_order(hist[None])[0].astype(np.uint8), hist, R, edge
 
 

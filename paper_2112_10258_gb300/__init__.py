@@ -109,6 +109,22 @@ class Sift3D:
         self._check(rc, "sift3d_describe")
         return brief, rrief
 
+    def describe_siftrank(self, kps, n: int = -1, stream=None, desc=None, rot=None, n_alloc: int | None = None,
+                          with_rotation: bool = False):
+        """3D SIFT-Rank descriptors (n x 64 uint8 ranks) of keypoints of the last
+        detect; with_rotation also returns the n x 9 keypoint frames."""
+        import torch
+        cap = n_alloc if n_alloc is not None else (n if n >= 0 else kps.numel() // 48)
+        dev = kps.device
+        if desc is None:
+            desc = torch.empty(max(cap, 1) * 64, dtype=torch.uint8, device=dev)
+        if with_rotation and rot is None:
+            rot = torch.empty(max(cap, 1) * 9, dtype=torch.float32, device=dev)
+        rc = capi.sift3d_describe_siftrank(self.ctx, kps.data_ptr(), n, desc.data_ptr(),
+                                           rot.data_ptr() if rot is not None else 0, _stream_handle(stream))
+        self._check(rc, "sift3d_describe_siftrank")
+        return (desc, rot) if with_rotation else desc
+
     def gaussian_blur(self, vol, sigma: float, out=None, stream=None):
         """Separable 3D Gaussian blur of a dense float32 CUDA tensor (nz, ny, nx)."""
         import torch

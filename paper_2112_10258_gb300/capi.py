@@ -106,6 +106,7 @@ SIGNATURES = {
                                         C.POINTER(C.c_int)]),
     "sift3d_match": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
+    "sift3d_describe_siftrank": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -243,3 +244,8 @@ def sift3d_match(dev_a: int, na: int, dev_b: int, nb: int, kind: int, dev_nn: in
     """Nearest-neighbour matching; pointers are device addresses (0 = NULL)."""
     return _lib.sift3d_match(C.c_void_p(dev_a), na, C.c_void_p(dev_b), nb, kind, C.c_void_p(dev_nn),
                              C.c_void_p(dev_dist), C.c_void_p(dev_dist2), C.c_void_p(stream))
+
+
+def sift3d_describe_siftrank(ctx, dev_kps: int, n: int, dev_desc: int, dev_rot: int, stream: int) -> int:
+    return _lib.sift3d_describe_siftrank(C.c_void_p(ctx), C.c_void_p(dev_kps), n, C.c_void_p(dev_desc),
+                                         C.c_void_p(dev_rot), C.c_void_p(stream))

@@ -543,6 +543,25 @@ int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int 
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
 }
 
+int sift3d_describe_siftrank(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, uint8_t* dev_desc,
+                             float* dev_rot, void* stream) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (!ctx->last) return set_err(ctx, SIFT3D_EINVAL, "describe needs a prior detect");
+    if (!dev_desc) return set_err(ctx, SIFT3D_EINVAL, "dev_desc is NULL");
+    if (n < -1) return set_err(ctx, SIFT3D_EINVAL, "n must be >= -1");
+    if (n != 0 && !dev_kps) return set_err(ctx, SIFT3D_EINVAL, "dev_kps is NULL");
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    const Workspace& ws = ctx->last->ws;
+    if (ws.plan.nO == 0) return SIFT3D_OK;
+    DescribeArgs d = make_describe_args(ws, ctx->pattern);
+    for (int o = 0; o < ws.plan.nO; ++o)            // the Gaussian levels themselves
+        for (int s = 1; s <= ws.plan.S; ++s) d.lv[o][s - 1].ptr = ws.G(o, s);
+    rc = enqueue_siftrank(ws.plan.p.storage, d, dev_kps, n, ws.count_out, ws.capacity, dev_desc, dev_rot,
+                          static_cast<cudaStream_t>(stream));
+    return rc == SIFT3D_OK ? rc : set_err(ctx, rc, "siftrank launch failed");
+}
+
 int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, int nz, double sigma,
                          float* dev_out, void* stream) {
     if (!ctx) return SIFT3D_EINVAL;

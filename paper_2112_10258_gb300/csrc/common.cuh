@@ -210,6 +210,9 @@ LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
 LaunchSpec match_spec(int kind, const MatchArgs& a);
+// SIFT-Rank descriptors of keypoints on the levels of d.lv (G_s, not pre-blurred).
+int enqueue_siftrank(int storage, const DescribeArgs& d, const sift3d_keypoint* kps, int n, const int* n_dev,
+                     int n_cap, uint8_t* desc, float* rot, cudaStream_t st);
 LaunchSpec tail_spec(int storage, const TailArgs& a);
 int tail_cluster_size(int storage, const TailArgs& a);   // 16, 8, or 0 (cannot run)
 // Row pitch of the small-octave kernel's shared slabs (odd: conflict-free columns).

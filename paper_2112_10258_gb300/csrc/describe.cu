@@ -7,6 +7,9 @@
 // (ties by lower index) by streaming the other 63 values through warp shuffles.
 // The 64-pair pattern sits in shared memory (lanes read different pairs, which
 // the constant cache would serialise).
+#include <algorithm>
+#include <cmath>
+
 #include "common.cuh"
 
 namespace sift3d {
@@ -100,6 +103,193 @@ __global__ void __launch_bounds__(DS_THREADS) describe_kernel(const DescribeArgs
     }
 }
 
+// ---- 3D SIFT-Rank (the paper's comparison baseline; Sec. 1 and Sec. 3.5) -----
+// One CTA per keypoint, on the keypoint's Gaussian level G_s (not pre-blurred).
+//   samples    the 8^3 cell centres of [-r, r]^3 (r = 3 sigma_s) inside the
+//              ball |u| <= r (280 of them), weight exp(-|u|^2 / (2 (r/2)^2));
+//   gradient   central differences of trilinear samples, unit steps;
+//   frame      e1 = mean gradient of the peak bin of the 12-direction
+//              (icosahedron) histogram of w |g|; e2 the same for the parts of
+//              the gradients perpendicular to e1; e3 = e1 x e2;
+//   histogram  samples at c + R u, g' = R^T g; element 8 * octant(u) +
+//              octant(g') gets w |g'|;
+//   output     the ranks of the 64 values (ties by lower index), as RRIEF.
+// Every sum runs over the samples in a fixed order, so the descriptor does
+// not depend on scheduling.
+constexpr int SR_THREADS = 128;
+constexpr int SR_MAX_SAMPLES = 512;
+
+struct SiftRankArgs {
+    const sift3d_keypoint* kps;
+    int n;                     // >= 0: count; < 0: read *n_dev, clamp to n_cap
+    const int* n_dev;
+    int n_cap;
+    int n_scales, n_octaves;
+    DescLevel lv[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES];   // G_s (not pre-blurred)
+    uint8_t* desc;             // n x 64 ranks
+    float* rot;                // n x 9 (row-major R, columns e1 e2 e3) or null
+    float ico[12][3];          // the icosahedron's unit vertices
+};
+
+template <typename S>
+__device__ __forceinline__ void gradient_at(const DescLevel& L, int cx, int cy, int cz, float tx, float ty, float tz,
+                                            float* g) {
+    g[0] = 0.5f * (sample<S>(L, cx, cy, cz, tx + 1.f, ty, tz) - sample<S>(L, cx, cy, cz, tx - 1.f, ty, tz));
+    g[1] = 0.5f * (sample<S>(L, cx, cy, cz, tx, ty + 1.f, tz) - sample<S>(L, cx, cy, cz, tx, ty - 1.f, tz));
+    g[2] = 0.5f * (sample<S>(L, cx, cy, cz, tx, ty, tz + 1.f) - sample<S>(L, cx, cy, cz, tx, ty, tz - 1.f));
+}
+
+__device__ __forceinline__ int nearest_direction(const float (*ico)[3], const float* v) {
+    int best = 0;
+    float bd = -INFINITY;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+        const float d = v[0] * ico[m][0] + v[1] * ico[m][1] + v[2] * ico[m][2];
+        if (d > bd) {
+            bd = d;
+            best = m;
+        }
+    }
+    return best;
+}
+
+// Peak bin of the 12-direction histogram of w |v| over the samples and the
+// weighted mean of that bin's vectors (fixed summation order).
+__device__ void direction_peak(int ns, const float (*vec)[3], const float* w, const int* bin, float* hist,
+                               float* mean) {
+    const int t = threadIdx.x;
+    if (t < 12) {
+        float h = 0.f;
+        for (int i = 0; i < ns; ++i)
+            if (bin[i] == t) h += w[i] * sqrtf(vec[i][0] * vec[i][0] + vec[i][1] * vec[i][1] + vec[i][2] * vec[i][2]);
+        hist[t] = h;
+    }
+    __syncthreads();
+    int m = 0;
+    for (int k = 1; k < 12; ++k)
+        if (hist[k] > hist[m]) m = k;
+    if (t < 3) {
+        float acc = 0.f;
+        for (int i = 0; i < ns; ++i)
+            if (bin[i] == m) acc += w[i] * vec[i][t];
+        mean[t] = acc;
+    }
+    __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(SR_THREADS) siftrank_kernel(const SiftRankArgs a) {
+    __shared__ float su[SR_MAX_SAMPLES][3];    // unit-radius sample offsets
+    __shared__ float sw[SR_MAX_SAMPLES];
+    __shared__ float sg[SR_MAX_SAMPLES][3];    // gradients (then perpendicular parts)
+    __shared__ int sb[SR_MAX_SAMPLES];
+    __shared__ float hist[64];
+    __shared__ float mean[3];
+    __shared__ float R[3][3];                  // columns e1 e2 e3: R[row][col]
+    __shared__ int nsamp;
+    const int t = threadIdx.x;
+    if (t == 0) {   // the fixed sample set (scale free: offsets in units of r)
+        int k = 0;
+        for (int z = 0; z < 8; ++z)
+            for (int y = 0; y < 8; ++y)
+                for (int x = 0; x < 8; ++x) {
+                    const float ux = ((x + 0.5f) / 8.f) * 2.f - 1.f, uy = ((y + 0.5f) / 8.f) * 2.f - 1.f;
+                    const float uz = ((z + 0.5f) / 8.f) * 2.f - 1.f;
+                    const float q = ux * ux + uy * uy + uz * uz;
+                    if (q <= 1.f) {
+                        su[k][0] = ux, su[k][1] = uy, su[k][2] = uz;
+                        sw[k] = expf(-q / (2.f * 0.25f));   // exp(-|u|^2 / (2 (r/2)^2)), |u| in units of r
+                        ++k;
+                    }
+                }
+        nsamp = k;
+    }
+    __syncthreads();
+    const int ns = nsamp;
+    const int n = a.n >= 0 ? a.n : min(*a.n_dev, a.n_cap);
+    for (int kp = blockIdx.x; kp < n; kp += gridDim.x) {
+        const sift3d_keypoint K = a.kps[kp];
+        if (K.octave < 0 || K.octave >= a.n_octaves || K.scale < 1 || K.scale > a.n_scales) continue;
+        const DescLevel& L = a.lv[K.octave][K.scale - 1];
+        const float r = 3.0f * L.sigma;
+        // primary direction
+        for (int i = t; i < ns; i += SR_THREADS) {
+            gradient_at<S>(L, K.ix, K.iy, K.iz, r * su[i][0], r * su[i][1], r * su[i][2], sg[i]);
+            sb[i] = nearest_direction(a.ico, sg[i]);
+        }
+        __syncthreads();
+        direction_peak(ns, sg, sw, sb, hist, mean);
+        if (t == 0) {
+            const float nm = sqrtf(mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2]);
+            if (nm > 0.f) {
+                R[0][0] = mean[0] / nm, R[1][0] = mean[1] / nm, R[2][0] = mean[2] / nm;
+            } else {
+                R[0][0] = 1.f, R[1][0] = 0.f, R[2][0] = 0.f;
+            }
+        }
+        __syncthreads();
+        const float e1x = R[0][0], e1y = R[1][0], e1z = R[2][0];
+        // secondary direction from the parts perpendicular to e1
+        for (int i = t; i < ns; i += SR_THREADS) {
+            const float d = sg[i][0] * e1x + sg[i][1] * e1y + sg[i][2] * e1z;
+            sg[i][0] -= d * e1x;
+            sg[i][1] -= d * e1y;
+            sg[i][2] -= d * e1z;
+            sb[i] = nearest_direction(a.ico, sg[i]);
+        }
+        __syncthreads();
+        direction_peak(ns, sg, sw, sb, hist, mean);
+        if (t == 0) {
+            float m0 = mean[0], m1 = mean[1], m2 = mean[2];
+            const float d = m0 * e1x + m1 * e1y + m2 * e1z;
+            m0 -= d * e1x, m1 -= d * e1y, m2 -= d * e1z;
+            float nm = sqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+            if (!(nm > 0.f)) {   // any axis perpendicular to e1
+                const bool px = fabsf(e1x) < 0.9f;
+                m0 = px ? 0.f : -e1z, m1 = px ? e1z : 0.f, m2 = px ? -e1y : e1x;
+                nm = sqrtf(m0 * m0 + m1 * m1 + m2 * m2);
+            }
+            R[0][1] = m0 / nm, R[1][1] = m1 / nm, R[2][1] = m2 / nm;
+            R[0][2] = e1y * R[2][1] - e1z * R[1][1];
+            R[1][2] = e1z * R[0][1] - e1x * R[2][1];
+            R[2][2] = e1x * R[1][1] - e1y * R[0][1];
+        }
+        __syncthreads();
+        // descriptor: samples at c + R u, gradients in the keypoint frame
+        for (int i = t; i < ns; i += SR_THREADS) {
+            const float ux = r * su[i][0], uy = r * su[i][1], uz = r * su[i][2];
+            const float tx = R[0][0] * ux + R[0][1] * uy + R[0][2] * uz;
+            const float ty = R[1][0] * ux + R[1][1] * uy + R[1][2] * uz;
+            const float tz = R[2][0] * ux + R[2][1] * uy + R[2][2] * uz;
+            float g[3];
+            gradient_at<S>(L, K.ix, K.iy, K.iz, tx, ty, tz, g);
+            const float gx = R[0][0] * g[0] + R[1][0] * g[1] + R[2][0] * g[2];
+            const float gy = R[0][1] * g[0] + R[1][1] * g[1] + R[2][1] * g[2];
+            const float gz = R[0][2] * g[0] + R[1][2] * g[1] + R[2][2] * g[2];
+            const int spatial = (su[i][0] >= 0.f) + 2 * (su[i][1] >= 0.f) + 4 * (su[i][2] >= 0.f);
+            const int orient = (gx >= 0.f) + 2 * (gy >= 0.f) + 4 * (gz >= 0.f);
+            sb[i] = 8 * spatial + orient;
+            sg[i][0] = sw[i] * sqrtf(gx * gx + gy * gy + gz * gz);
+        }
+        __syncthreads();
+        if (t < 64) {
+            float h = 0.f;
+            for (int i = 0; i < ns; ++i)
+                if (sb[i] == t) h += sg[i][0];
+            hist[t] = h;
+        }
+        __syncthreads();
+        if (t < 64) {
+            const float v = hist[t];
+            int rank = 0;
+            for (int j = 0; j < 64; ++j) rank += (hist[j] < v) || (hist[j] == v && j < t);
+            a.desc[(int64_t)kp * 64 + t] = (uint8_t)rank;
+        }
+        if (a.rot != nullptr && t < 9) a.rot[(int64_t)kp * 9 + t] = R[t / 3][t % 3];
+        __syncthreads();
+    }
+}
+
 template <typename S>
 __global__ void read_level_kernel(const ReadLevelArgs a) {
     const int64_t n = (int64_t)a.nx * a.ny * a.nz;
@@ -126,6 +316,39 @@ LaunchSpec describe_spec(int storage, const DescribeArgs&, int n_max) {
     s.smem = 0;
     s.name = "describe";
     return s;
+}
+
+int enqueue_siftrank(int storage, const DescribeArgs& d, const sift3d_keypoint* kps, int n, const int* n_dev,
+                     int n_cap, uint8_t* desc, float* rot, cudaStream_t st) {
+    SiftRankArgs a{};
+    {   // cyclic permutations of (0, +-1, +-phi), normalised
+        const double phi = (1.0 + std::sqrt(5.0)) / 2.0, inv = 1.0 / std::sqrt(1.0 + phi * phi);
+        int k = 0;
+        for (double u : {1.0, -1.0})
+            for (double v : {phi, -phi}) a.ico[k][0] = 0.f, a.ico[k][1] = (float)(u * inv), a.ico[k][2] = (float)(v * inv), ++k;
+        for (double u : {1.0, -1.0})
+            for (double v : {phi, -phi}) a.ico[k][0] = (float)(u * inv), a.ico[k][1] = (float)(v * inv), a.ico[k][2] = 0.f, ++k;
+        for (double u : {1.0, -1.0})
+            for (double v : {phi, -phi}) a.ico[k][0] = (float)(v * inv), a.ico[k][1] = 0.f, a.ico[k][2] = (float)(u * inv), ++k;
+    }
+    a.kps = kps;
+    a.n = n;
+    a.n_dev = n_dev;
+    a.n_cap = n_cap;
+    a.n_scales = d.n_scales;
+    a.n_octaves = d.n_octaves;
+    memcpy(a.lv, d.lv, sizeof(a.lv));
+    a.desc = desc;
+    a.rot = rot;
+    const void* f = storage == SIFT3D_STORAGE_F32   ? reinterpret_cast<const void*>(&siftrank_kernel<float>)
+                    : storage == SIFT3D_STORAGE_F16 ? reinterpret_cast<const void*>(&siftrank_kernel<__half>)
+                                                    : reinterpret_cast<const void*>(&siftrank_kernel<__nv_bfloat16>);
+    const int n_max = n >= 0 ? n : n_cap;
+    if (n_max <= 0) return SIFT3D_OK;
+    const int blocks = std::min(n_max, 8 * 152);
+    void* args[1] = {&a};
+    return cudaLaunchKernel(f, dim3(blocks), dim3(SR_THREADS), args, 0, st) == cudaSuccess ? SIFT3D_OK
+                                                                                           : SIFT3D_ECUDA;
 }
 
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a) {

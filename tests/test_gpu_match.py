@@ -93,12 +93,15 @@ def test_synthetic_pair_matching_inliers(S):
         buf, n = det.detect(torch.from_numpy(vol).cuda(), capacity=16384)
         kps = S.keypoints_to_numpy(buf, n)
         brief, rrief = det.describe(buf, n)
-        res.append((kps, brief[:n].clone(), rrief[: n * 64].clone().view(n, 64)))
+        sr = det.describe_siftrank(buf, n)
+        res.append((kps, brief[:n].clone(), rrief[: n * 64].clone().view(n, 64), sr[: n * 64].clone().view(n, 64)))
         det.close()
-    (ka, ba, ra), (kb, bb, rb) = res
+    (ka, ba, ra, sa), (kb, bb, rb, sb) = res
     assert ka.size > 200 and kb.size > 200
     report = {}
-    for kind, da, db in ((1, ba, bb), (2, ra, rb)):
+    for kind, da, db in ((1, ba, bb), (2, ra, rb), (3, sa, sb)):
+        name = kind
+        kind = min(kind, 2)                 # SIFT-Rank ranks use the rank distance
         nn, d1, d2 = (t.cpu().numpy() for t in S.match(da, db, kind))
         sel = np.arange(0, ka.size, max(1, ka.size // 60))
         ref = O.match((da.cpu().numpy().view(np.uint64) if kind == 1 else da.cpu().numpy())[sel],
@@ -112,9 +115,10 @@ def test_synthetic_pair_matching_inliers(S):
         dz = (ka["z"] - sz) - m["z"]
         close = np.maximum(np.abs(dx), np.maximum(np.abs(dy), np.abs(dz))) <= scale
         ratio = d1 < 0.8 * d2
-        report[kind] = (int(np.sum(same & close)), int(np.sum(same & close & ratio)), int(np.sum(ratio)), ka.size)
-    print("inliers (all NN, ratio-test NN, ratio-test matches, queries): BRIEF", report[1], "RRIEF", report[2])
-    for kind in (1, 2):
+        report[name] = (int(np.sum(same & close)), int(np.sum(same & close & ratio)), int(np.sum(ratio)), ka.size)
+    print("inliers (all NN, ratio-test NN, ratio-test matches, queries): BRIEF", report[1], "RRIEF", report[2],
+          "SIFT-Rank", report[3])
+    for kind in (1, 2, 3):
         inl, inl_r, n_r, nq = report[kind]
         assert inl >= 0.3 * nq                     # most shifted keypoints find their twin
         assert inl_r >= 0.8 * n_r                  # the ratio test keeps mostly inliers
