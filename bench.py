@@ -609,6 +609,27 @@ def main():
                        "sum_ms": tot, "step_ms": ms_per_step, "path_ms": path_ms}, f, indent=1)
     det_prof.close()
 
+    # ---- phase 3b: each descriptor alone on the headline volume's keypoints
+    # (the paper times SIFT-Rank, BRIEF and RRIEF separately)
+    desc_us = {}
+    det.detect(d_vol, capacity=CAPACITY, out=kbuf)
+    sr_out = torch.empty(CAPACITY * 64, dtype=torch.uint8, device="cuda")
+    runs = {"brief": lambda: det.describe(kbuf, -1, kind=S.DESC_BRIEF, brief=brief, rrief=rrief, n_alloc=CAPACITY),
+            "rrief": lambda: det.describe(kbuf, -1, kind=S.DESC_RRIEF, brief=brief, rrief=rrief, n_alloc=CAPACITY),
+            "siftrank": lambda: det.describe_siftrank(kbuf, -1, desc=sr_out, n_alloc=CAPACITY)}
+    for name, fn in runs.items():
+        for _ in range(args.warmup):
+            fn()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        desc_us[name] = 1e3 * e0.elapsed_time(e1) / args.steps
+
     # ---- phase 4: end to end through the public serving API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -668,6 +689,9 @@ def main():
                           "ms": path_ms, "achieved": path_gbs, "peak": peak, "unit": "GB/s",
                           "frac": path_gbs / peak, "peak_kind": peak_kind},
         "e2e": e2e, "cpu_baseline": base, "clocks": clk,
+        "descriptor_us": {"keypoints": n_kp, **desc_us,
+                          "note": "each descriptor alone (device count, no host wait), L2 warm; paper (GPU "
+                                  "not named): SIFT-Rank 51 ms, BRIEF 22 ms, RRIEF 25 ms"},
         "gpu_launches": args.steps * (n_detect_kernels + 1),
         "paper_context": {"seconds_per_volume": 0.2, "note": "paper: 1.4 s CPU -> 0.2 s GPU per 145x174x145 "
                                                              "OASIS volume with ~3000 keypoints, hardware not named"},
