@@ -128,12 +128,14 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
     if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
     // The small-octave kernel takes the longest run of last octaves (from
     // octave 1 on) of at most kTailMaxVoxels voxels whose z-slabs fit its
-    // shared memory: ceil(nz / 8) planes of each level per CTA.
+    // shared memory: ceil(nz / 16) planes of each level per CTA.
     pl.tail_start = pl.nO;
     if (p.fuse_small_octaves)
         for (int o = pl.nO - 1; o >= 1; --o) {
             const OctaveGeom& g = pl.oct[o];
-            const int slab = (g.nz + kTailClusterPortable - 1) / kTailClusterPortable;
+            // slabs for the 16-CTA cluster; a device that cannot hold it makes
+            // the detect fall back to separate launches (build_detect)
+            const int slab = (g.nz + kTailCluster - 1) / kTailCluster;
             const bool fits = slab <= kTailMaxSlab && g.voxels() <= kTailMaxVoxels &&
                               tail_smem_bytes(tail_row_pitch(g.nx) * g.ny, slab) <= kTailMaxSmem;
             if (!fits) break;

@@ -13,10 +13,11 @@
 //   cluster barrier
 //   z pass   T of this and the neighbouring CTAs  -> G_s (shared + global),
 //            read through distributed shared memory     D_{s-1} (global)
-// and the descriptor pre-blur B_s of G_s (Sec. 2.2.3) the same way.  T
-// alternates between two buffers, so one cluster barrier per pass suffices: a
-// CTA can only overwrite a T buffer after every CTA has passed the barrier that
-// follows the last read of it.  Every level, DoG and pre-blurred level is also
+// and, in the same phases, the descriptor pre-blur B_{s-1} of G_{s-1}
+// (Sec. 2.2.3) when s-1 is a detection scale.  T alternates between two
+// buffers, so one cluster barrier per level suffices: a CTA can only overwrite
+// a T buffer after every CTA has passed the barrier that follows the last read
+// of it.  Every level, DoG and pre-blurred level is also
 // written to its place in the workspace, where the peak kernels, describe and
 // sift3d_read_level find it.
 //
@@ -38,57 +39,12 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int CT = 512;               // threads per CTA
-constexpr int STRIP = 8;              // outputs per thread along the y and x passes
 constexpr int MAXP = kTailMaxSlab;    // planes per CTA slab
 
-// Taps of the pass being run, copied to shared memory so that strip functions
-// can hold them in registers by compile-time index.
+// Taps of the pass being run, in shared memory (w[k] = w_|k|).
 struct PassTaps {
     float w[kMaxRadius + 1];
 };
-
-template <int R>
-__device__ __forceinline__ void load_taps(const PassTaps& t, float (&w)[R + 1]) {
-#pragma unroll
-    for (int k = 0; k <= R; ++k) w[k] = t.w[k];
-}
-
-// y pass of one column strip: rows r0 .. r0+7 of column x of one plane.
-template <int R>
-__device__ __forceinline__ void y_strip(const float* src, float* dst, int py, int ny, int x, int r0,
-                                        const PassTaps& t) {
-    float w[R + 1];
-    load_taps<R>(t, w);
-    float v[STRIP + 2 * R];
-#pragma unroll
-    for (int i = 0; i < STRIP + 2 * R; ++i) v[i] = src[min(max(r0 - R + i, 0), ny - 1) * py + x];
-#pragma unroll
-    for (int j = 0; j < STRIP; ++j) {
-        if (r0 + j >= ny) break;
-        float acc = 0.f;
-#pragma unroll
-        for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
-        dst[(r0 + j) * py + x] = acc;
-    }
-}
-
-// x pass of one row strip: columns c0 .. c0+7 of one row.
-template <int R>
-__device__ __forceinline__ void x_strip(const float* src, float* dst, int nx, int c0, const PassTaps& t) {
-    float w[R + 1];
-    load_taps<R>(t, w);
-    float v[STRIP + 2 * R];
-#pragma unroll
-    for (int i = 0; i < STRIP + 2 * R; ++i) v[i] = src[min(max(c0 - R + i, 0), nx - 1)];
-#pragma unroll
-    for (int j = 0; j < STRIP; ++j) {
-        if (c0 + j >= nx) break;
-        float acc = 0.f;
-#pragma unroll
-        for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
-        dst[c0 + j] = acc;
-    }
-}
 
 // Geometry of the current octave as seen by one CTA.  The shared slabs use an
 // odd row pitch (nx | 1), so the lanes of a warp reading one column each (the x
@@ -102,24 +58,33 @@ struct Slab {
 
 __device__ __forceinline__ int slab_begin(int k, int nz, int ncta) { return (k * nz) / ncta; }
 
-// y then x pass of the CTA's own planes: src (shared, float) -> dst (shared).
-// U is the scratch plane set between the passes.
-template <int R>
-__device__ void xy_pass(const Slab& g, const float* src, float* U, float* dst, const PassTaps& t) {
-    const int ystrips = (g.ny + STRIP - 1) / STRIP;
-    for (int i = threadIdx.x; i < g.n * g.nx * ystrips; i += CT) {
+// The passes below loop over the taps at run time and read every tap from
+// (distributed) shared memory: the octaves this kernel takes are small, so the
+// loads cost little, and one compact body serves every radius (fully unrolled
+// per-radius bodies measured slower here: each pass jumped into cold code).
+// Every output is acc = fmaf(w_|k|, in[clamp(i + k)], acc) for k = -R..R from
+// 0, the chain the separate kernels compute.
+
+// y then x pass of the CTA's own planes: src (shared) -> U (shared) -> dst (shared).
+__device__ void xy_pass(const Slab& g, const float* src, float* U, float* dst, const PassTaps& t, int R) {
+    for (int i = threadIdx.x; i < g.n * g.nx * g.ny; i += CT) {
         const int x = i % g.nx;
         const int rest = i / g.nx;
-        const int rs = rest % ystrips, lz = rest / ystrips;
-        y_strip<R>(src + lz * g.P, U + lz * g.P, g.py, g.ny, x, rs * STRIP, t);
+        const int y = rest % g.ny, lz = rest / g.ny;
+        const float* col = src + lz * g.P + x;
+        float acc = 0.f;
+        for (int k = -R; k <= R; ++k) acc = fmaf(t.w[k < 0 ? -k : k], col[min(max(y + k, 0), g.ny - 1) * g.py], acc);
+        U[lz * g.P + y * g.py + x] = acc;
     }
     __syncthreads();
-    const int xstrips = (g.nx + STRIP - 1) / STRIP;
-    for (int i = threadIdx.x; i < g.n * g.ny * xstrips; i += CT) {
-        const int y = i % g.ny;            // lanes on consecutive rows: odd pitch, no bank conflict
-        const int rest = i / g.ny;
-        const int xs = rest % xstrips, lz = rest / xstrips;
-        x_strip<R>(U + lz * g.P + y * g.py, dst + lz * g.P + y * g.py, g.nx, xs * STRIP, t);
+    for (int i = threadIdx.x; i < g.n * g.nx * g.ny; i += CT) {
+        const int x = i % g.nx;
+        const int rest = i / g.nx;
+        const int y = rest % g.ny, lz = rest / g.ny;
+        const float* row = U + lz * g.P + y * g.py;
+        float acc = 0.f;
+        for (int k = -R; k <= R; ++k) acc = fmaf(t.w[k < 0 ? -k : k], row[min(max(x + k, 0), g.nx - 1)], acc);
+        dst[lz * g.P + y * g.py + x] = acc;
     }
 }
 
@@ -127,8 +92,9 @@ __device__ void xy_pass(const Slab& g, const float* src, float* U, float* dst, c
 // and its neighbours, through distributed shared memory).  For every output
 // voxel calls out(lz, shared offset in the plane, global offset in the plane,
 // value); gpy is the global row pitch.
-template <int R, class Out>
-__device__ void z_pass(const Slab& g, int64_t gpy, float* T, const PassTaps& t, const float** zplane, Out out) {
+template <class Out>
+__device__ void z_pass(const Slab& g, int64_t gpy, float* T, const PassTaps& t, const float** zplane, int R,
+                       Out out) {
     cg::cluster_group cluster = cg::this_cluster();
     // Input plane q of this CTA's window is plane z = clamp(z0 - R + q) of the
     // octave, held by the CTA k that owns z (the largest k with
@@ -140,47 +106,16 @@ __device__ void z_pass(const Slab& g, int64_t gpy, float* T, const PassTaps& t, 
         zplane[threadIdx.x] = cluster.map_shared_rank(T, k) + (z - slab_begin(k, g.nz, g.ncta)) * g.P;
     }
     __syncthreads();
-    float w[R + 1];
-    load_taps<R>(t, w);
-    const int cols = g.nx * g.ny;
-    for (int i = threadIdx.x; i < cols; i += CT) {
-        const int x = i % g.nx, y = i / g.nx;
+    for (int i = threadIdx.x; i < g.n * g.nx * g.ny; i += CT) {
+        const int x = i % g.nx;
+        const int rest = i / g.nx;
+        const int y = rest % g.ny, j = rest / g.ny;
         const int off = y * g.py + x;
-        float v[MAXP + 2 * R];
-#pragma unroll
-        for (int q = 0; q < MAXP + 2 * R; ++q) v[q] = q < g.n + 2 * R ? zplane[q][off] : 0.f;
-        const int64_t goff = (int64_t)y * gpy + x;
-#pragma unroll
-        for (int j = 0; j < MAXP; ++j) {
-            if (j >= g.n) break;
-            float acc = 0.f;
-#pragma unroll
-            for (int k = -R; k <= R; ++k) acc = fmaf(w[k < 0 ? -k : k], v[j + R + k], acc);
-            out(j, off, goff, acc);
-        }
+        float acc = 0.f;
+        for (int k = -R; k <= R; ++k) acc = fmaf(t.w[k < 0 ? -k : k], zplane[j + R + k][off], acc);
+        out(j, off, (int64_t)y * gpy + x, acc);
     }
 }
-
-// Dispatch on the radius (only radii of the schedule are ever hot).
-#define SIFT3D_RADIUS_SWITCH(R_RUNTIME, CALL)                          \
-    switch (R_RUNTIME) {                                              \
-        case 1: { constexpr int RR = 1; CALL; } break;                \
-        case 2: { constexpr int RR = 2; CALL; } break;                \
-        case 3: { constexpr int RR = 3; CALL; } break;                \
-        case 4: { constexpr int RR = 4; CALL; } break;                \
-        case 5: { constexpr int RR = 5; CALL; } break;                \
-        case 6: { constexpr int RR = 6; CALL; } break;                \
-        case 7: { constexpr int RR = 7; CALL; } break;                \
-        case 8: { constexpr int RR = 8; CALL; } break;                \
-        case 9: { constexpr int RR = 9; CALL; } break;                \
-        case 10: { constexpr int RR = 10; CALL; } break;              \
-        case 11: { constexpr int RR = 11; CALL; } break;              \
-        case 12: { constexpr int RR = 12; CALL; } break;              \
-        case 13: { constexpr int RR = 13; CALL; } break;              \
-        case 14: { constexpr int RR = 14; CALL; } break;              \
-        case 15: { constexpr int RR = 15; CALL; } break;              \
-        default: { constexpr int RR = 16; CALL; } break;              \
-    }
 
 template <typename S>
 __device__ __forceinline__ float ld_s(const S* p) { return to_f32(*p); }
@@ -206,7 +141,7 @@ __device__ __forceinline__ float sub_mean_cg(const S* p, int64_t py, int64_t pz)
 template <typename S>
 __global__ void __launch_bounds__(CT, 1) tail_kernel(const __grid_constant__ TailArgs a) {
     extern __shared__ __align__(16) float tl_sm[];
-    __shared__ PassTaps taps;
+    __shared__ PassTaps taps, taps2;
     __shared__ const float* zplane[MAXP + 2 * kMaxRadius];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -229,7 +164,9 @@ __global__ void __launch_bounds__(CT, 1) tail_kernel(const __grid_constant__ Tai
         float* Gprev = tl_sm;
         float* Gcur = tl_sm + SL;
         float* U = tl_sm + 2 * SL;
-        float* Tb[2] = {tl_sm + 3 * SL, tl_sm + 4 * SL};
+        float* U2 = tl_sm + 3 * SL;
+        float* Tb[2] = {tl_sm + 4 * SL, tl_sm + 5 * SL};
+        float* T2b[2] = {tl_sm + 6 * SL, tl_sm + 7 * SL};
         int tb = 0;
 
         // ---- level 1 from the sub-sampled level S of the previous octave
@@ -274,45 +211,45 @@ __global__ void __launch_bounds__(CT, 1) tail_kernel(const __grid_constant__ Tai
             }
         }
         for (int s = 1; s < a.L; ++s) {
-            if (threadIdx.x <= kMaxRadius) taps.w[threadIdx.x] = a.t_inc[s - 1].w[threadIdx.x];
+            // Level s also pre-blurs G_{s-1} for the descriptors when s-1 is a
+            // detection scale (as the separate level kernels do), so each
+            // level is one y/x phase, one cluster barrier and one z phase.
+            const bool blur = a.r_desc > 0 && s >= 2 && s - 1 <= a.S;
+            if (threadIdx.x <= kMaxRadius) {
+                taps.w[threadIdx.x] = a.t_inc[s - 1].w[threadIdx.x];
+                taps2.w[threadIdx.x] = a.t_desc.w[threadIdx.x];
+            }
             __syncthreads();
             float* T = Tb[tb];
+            float* T2 = T2b[tb];
             const int R = a.r_inc[s - 1];
             // level 1 filters the unrounded mean held in Gcur, later levels G_{s-1}
             const float* xsrc = s == 1 ? Gcur : Gprev;
-            SIFT3D_RADIUS_SWITCH(R, (xy_pass<RR>(g, xsrc, U, T, taps)));
+            xy_pass(g, xsrc, U, T, taps, R);
+            if (blur) xy_pass(g, Gprev, U2, T2, taps2, a.r_desc);
             cluster.sync();
             S* Gs = static_cast<S*>(o.G[s]);
             S* Ds = static_cast<S*>(o.D[s - 1]);
             const int64_t zoff = (int64_t)g.z0 * o.pz;
-            SIFT3D_RADIUS_SWITCH(R, (z_pass<RR>(g, o.py, T, taps, zplane,
-                                                [&](int j, int off, int64_t goff, float acc) {
-                                                    const S gs = from_f32<S>(acc);
-                                                    const int li = j * g.P + off;
-                                                    Gs[zoff + (int64_t)j * o.pz + goff] = gs;
-                                                    Ds[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(Gprev[li] - acc);
-                                                    Gcur[li] = to_f32(gs);
-                                                })));
+            z_pass(g, o.py, T, taps, zplane, R, [&](int j, int off, int64_t goff, float acc) {
+                const S gs = from_f32<S>(acc);
+                const int li = j * g.P + off;
+                Gs[zoff + (int64_t)j * o.pz + goff] = gs;
+                Ds[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(Gprev[li] - acc);
+                Gcur[li] = to_f32(gs);
+            });
+            if (blur) {
+                __syncthreads();   // the plane table is rebuilt for T2
+                S* Bs = static_cast<S*>(o.B[s - 2]);
+                z_pass(g, o.py, T2, taps2, zplane, a.r_desc, [&](int j, int, int64_t goff, float acc) {
+                    Bs[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(acc);
+                });
+            }
             __syncthreads();
             float* t = Gprev;   // G_s becomes the next level's source
             Gprev = Gcur;
             Gcur = t;
             tb ^= 1;
-            // descriptor pre-blur of G_s, s = 1..S
-            if (a.r_desc > 0 && s <= a.S) {
-                if (threadIdx.x <= kMaxRadius) taps.w[threadIdx.x] = a.t_desc.w[threadIdx.x];
-                __syncthreads();
-                float* T2 = Tb[tb];
-                SIFT3D_RADIUS_SWITCH(a.r_desc, (xy_pass<RR>(g, Gprev, U, T2, taps)));
-                cluster.sync();
-                S* Bs = static_cast<S*>(o.B[s - 1]);
-                SIFT3D_RADIUS_SWITCH(a.r_desc, (z_pass<RR>(g, o.py, T2, taps, zplane,
-                                                           [&](int j, int, int64_t goff, float acc) {
-                                                               Bs[zoff + (int64_t)j * o.pz + goff] = from_f32<S>(acc);
-                                                           })));
-                __syncthreads();
-                tb ^= 1;
-            }
         }
         // the next octave sub-samples this octave's level S, written by every
         // CTA: all stores before this barrier are visible after it
@@ -395,7 +332,7 @@ int tail_cluster_size(int storage, const TailArgs& a) {
 }
 
 size_t tail_smem_bytes(int plane_elems, int slab_planes) {
-    return (size_t)5 * slab_planes * plane_elems * sizeof(float);
+    return (size_t)8 * slab_planes * plane_elems * sizeof(float);   // G_{s-1}, G_s, 2 y scratch, 2 x 2 T
 }
 
 }  // namespace sift3d
