@@ -215,13 +215,27 @@ def _dist_setup(world, local):
     return dist
 
 
-def _max_over_ranks(dist, v):
+def _max_over_ranks(dist, v, device="cuda"):
+    """The largest v over all ranks (the job's time is its slowest rank); the
+    only collective of a multi-rank run, outside the timed region."""
     import torch
     if dist is None:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_volume_seed(rank: int) -> int:
+    """Each rank processes its own synthetic volume (weak scaling: the units of
+    work are independent volumes, no data moves between ranks)."""
+    return rank
+
+
+def whole_job_value(world: int, steps: int, voxels_per_step: int, total_ms: float) -> float:
+    """Voxels per second of the whole job: every rank processed steps volumes of
+    voxels_per_step voxels in at most total_ms (the max over ranks)."""
+    return world * steps * voxels_per_step / (total_ms / 1e3)
 
 
 # ---------------------------------------------------------------- batched mode
@@ -460,7 +474,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     storage = {"f32": S.STORAGE_F32, "f16": S.STORAGE_F16, "bf16": S.STORAGE_BF16}[args.storage]
 
-    vol = brain_like_volume(seed=rank)
+    vol = brain_like_volume(seed=rank_volume_seed(rank))
     nx, ny, nz = SHAPE
     voxels = vol.size
     d_vol = torch.from_numpy(vol).cuda()
@@ -486,11 +500,7 @@ def main():
         return [a.elapsed_time(b) for a, b in evs]
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return _max_over_ranks(dist, v)
 
     # ---- phase 1: the full hot path (detect + describe), graph launch path
     use_graphs = 0 if args.eager else 1
@@ -553,7 +563,7 @@ def main():
         total_ms = max_over_ranks(e0.elapsed_time(e1))
         l2_note = f"inputs larger than L2: {len(pool)} distinct resident volumes ({len(pool) * vol.nbytes >> 20} MiB)"
     ms_per_step = total_ms / args.steps
-    value = world * args.steps * voxels / (total_ms / 1e3)
+    value = whole_job_value(world, args.steps, voxels, total_ms)
     if args.only == "detect":
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
