@@ -23,8 +23,14 @@ blocking or fusion:
   2.2.2 "4D Peak Detection" (sum-of-signs equation).  The extremum search here is
   the brute-force neighbour comparison the paper's CPU method uses (Sec. 4.4).
 * BRIEF (binarised point-pair differences of a blurred patch) and RRIEF (the same
-  differences, rank ordered) - Sec. 2.2.3; point-pair method 3 (p1 ~ N(0, s),
-  p2 ~ N(p1, s)); pre-blur sigma 0.95 (Sec. 4.5).
+  differences, rank ordered) - Sec. 2.2.3; point-pair methods 1-5 (method 3,
+  p1 ~ N(0, s), p2 ~ N(p1, s), by default); pre-blur sigma 0.95 (Sec. 4.5).
+* Nearest-neighbour matching of descriptors - Sec. 2.1 (e).
+* The 3D SIFT-Rank descriptor, the paper's comparison baseline, which the paper
+  only outlines (Sec. 1: spherical gradient histogram orientation, 2x2x2 x 8
+  bins, rank normalisation); the details are this implementation's reading.
+* Sub-voxel refinement (one Newton step on the 4D DoG quadratic): not in the
+  paper.
 
 Readings where the paper is silent (each also listed in the design doc):
 
