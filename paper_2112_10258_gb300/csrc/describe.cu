@@ -114,10 +114,16 @@ __global__ void __launch_bounds__(DS_THREADS) describe_kernel(const DescribeArgs
 //   histogram  samples at c + R u, g' = R^T g; element 8 * octant(u) +
 //              octant(g') gets w |g'|;
 //   output     the ranks of the 64 values (ties by lower index), as RRIEF.
-// Every sum runs over the samples in a fixed order, so the descriptor does
-// not depend on scheduling.
+// Sample i belongs to thread i % SR_THREADS.  The 12-direction histograms and
+// the bin means are per-thread partials reduced by a fixed xor butterfly in
+// each warp and then warp by warp in index order; the 64-bin histogram sums
+// each bin over its spatial octant's samples (the table is ordered by octant)
+// in table order.  Every sum has a fixed order, so the descriptor does not
+// depend on scheduling.
 constexpr int SR_THREADS = 128;
-constexpr int SR_MAX_SAMPLES = 512;
+constexpr int SR_WARPS = SR_THREADS / 32;
+constexpr int SR_SAMPLES = 280;        // cell centres of the 8^3 grid on [-1, 1]^3 inside the unit ball
+constexpr int SR_SLOTS = (SR_SAMPLES + SR_THREADS - 1) / SR_THREADS;
 
 struct SiftRankArgs {
     const sift3d_keypoint* kps;
@@ -129,6 +135,8 @@ struct SiftRankArgs {
     uint8_t* desc;             // n x 64 ranks
     float* rot;                // n x 9 (row-major R, columns e1 e2 e3) or null
     float ico[12][3];          // the icosahedron's unit vertices
+    int oct_start[9];          // samples of spatial octant o: [oct_start[o], oct_start[o + 1])
+    float smp[SR_SAMPLES][4];  // the samples by octant: offset in units of r (x, y, z) and weight
 };
 
 template <typename S>
@@ -153,92 +161,108 @@ __device__ __forceinline__ int nearest_direction(const float (*ico)[3], const fl
     return best;
 }
 
-// Peak bin of the 12-direction histogram of w |v| over the samples and the
-// weighted mean of that bin's vectors (fixed summation order).
-__device__ void direction_peak(int ns, const float (*vec)[3], const float* w, const int* bin, float* hist,
-                               float* mean) {
-    const int t = threadIdx.x;
-    if (t < 12) {
-        float h = 0.f;
-        for (int i = 0; i < ns; ++i)
-            if (bin[i] == t) h += w[i] * sqrtf(vec[i][0] * vec[i][0] + vec[i][1] * vec[i][1] + vec[i][2] * vec[i][2]);
-        hist[t] = h;
-    }
+// Sum of v over the CTA, written to out[0..NV) for every thread to read.
+template <int NV>
+__device__ __forceinline__ void cta_sum(float (&v)[NV], float (*red)[16], float* out) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
     __syncthreads();
-    int m = 0;
-    for (int k = 1; k < 12; ++k)
-        if (hist[k] > hist[m]) m = k;
-    if (t < 3) {
-        float acc = 0.f;
-        for (int i = 0; i < ns; ++i)
-            if (bin[i] == m) acc += w[i] * vec[i][t];
-        mean[t] = acc;
+    if (t < NV) {
+        float acc = red[0][t];
+#pragma unroll
+        for (int w = 1; w < SR_WARPS; ++w) acc += red[w][t];
+        out[t] = acc;
     }
     __syncthreads();
 }
 
+// Peak bin of the 12-direction histogram of w |v| over the samples and the
+// weighted mean of that bin's vectors (mean[0..3) in shared memory).
+__device__ __forceinline__ void direction_peak(const float (*ico)[3], const float (&v)[SR_SLOTS][3],
+                                               const float (&w)[SR_SLOTS], float (*red)[16], float* hist,
+                                               float* mean) {
+    int b[SR_SLOTS];
+    float h[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) h[m] = 0.f;
+#pragma unroll
+    for (int j = 0; j < SR_SLOTS; ++j) {
+        b[j] = nearest_direction(ico, v[j]);
+        const float mag = w[j] * sqrtf(v[j][0] * v[j][0] + v[j][1] * v[j][1] + v[j][2] * v[j][2]);
+#pragma unroll
+        for (int m = 0; m < 12; ++m) h[m] += b[j] == m ? mag : 0.f;
+    }
+    cta_sum<12>(h, red, hist);
+    int m = 0;
+    for (int k = 1; k < 12; ++k)
+        if (hist[k] > hist[m]) m = k;
+    float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < SR_SLOTS; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += b[j] == m ? w[j] * v[j][c] : 0.f;
+    cta_sum<3>(acc, red, mean);
+}
+
 template <typename S>
-__global__ void __launch_bounds__(SR_THREADS) siftrank_kernel(const SiftRankArgs a) {
-    __shared__ float su[SR_MAX_SAMPLES][3];    // unit-radius sample offsets
-    __shared__ float sw[SR_MAX_SAMPLES];
-    __shared__ float sg[SR_MAX_SAMPLES][3];    // gradients (then perpendicular parts)
-    __shared__ int sb[SR_MAX_SAMPLES];
+__global__ void __launch_bounds__(SR_THREADS, 8) siftrank_kernel(const SiftRankArgs a) {
+    __shared__ float sval[SR_SAMPLES];      // w |g'| of each sample
+    __shared__ int sbin[SR_SAMPLES];        // its orientation octant
+    __shared__ float red[SR_WARPS][16];
     __shared__ float hist[64];
     __shared__ float mean[3];
-    __shared__ float R[3][3];                  // columns e1 e2 e3: R[row][col]
-    __shared__ int nsamp;
+    __shared__ float R[3][3];               // columns e1 e2 e3: R[row][col]
+    __shared__ float ico[12][3];
+    __shared__ int oct[9];
+    __shared__ float4 smp[SR_SAMPLES];
     const int t = threadIdx.x;
-    if (t == 0) {   // the fixed sample set (scale free: offsets in units of r)
-        int k = 0;
-        for (int z = 0; z < 8; ++z)
-            for (int y = 0; y < 8; ++y)
-                for (int x = 0; x < 8; ++x) {
-                    const float ux = ((x + 0.5f) / 8.f) * 2.f - 1.f, uy = ((y + 0.5f) / 8.f) * 2.f - 1.f;
-                    const float uz = ((z + 0.5f) / 8.f) * 2.f - 1.f;
-                    const float q = ux * ux + uy * uy + uz * uz;
-                    if (q <= 1.f) {
-                        su[k][0] = ux, su[k][1] = uy, su[k][2] = uz;
-                        sw[k] = expf(-q / (2.f * 0.25f));   // exp(-|u|^2 / (2 (r/2)^2)), |u| in units of r
-                        ++k;
-                    }
-                }
-        nsamp = k;
-    }
+    if (t < 36) ico[t / 3][t % 3] = a.ico[t / 3][t % 3];
+    if (t < 9) oct[t] = a.oct_start[t];
+    for (int i = t; i < SR_SAMPLES; i += SR_THREADS)   // unit-radius offsets and weights
+        smp[i] = make_float4(a.smp[i][0], a.smp[i][1], a.smp[i][2], a.smp[i][3]);
     __syncthreads();
-    const int ns = nsamp;
     const int n = a.n >= 0 ? a.n : min(*a.n_dev, a.n_cap);
     for (int kp = blockIdx.x; kp < n; kp += gridDim.x) {
         const sift3d_keypoint K = a.kps[kp];
         if (K.octave < 0 || K.octave >= a.n_octaves || K.scale < 1 || K.scale > a.n_scales) continue;
         const DescLevel& L = a.lv[K.octave][K.scale - 1];
         const float r = 3.0f * L.sigma;
-        // primary direction
-        for (int i = t; i < ns; i += SR_THREADS) {
-            gradient_at<S>(L, K.ix, K.iy, K.iz, r * su[i][0], r * su[i][1], r * su[i][2], sg[i]);
-            sb[i] = nearest_direction(a.ico, sg[i]);
-        }
-        __syncthreads();
-        direction_peak(ns, sg, sw, sb, hist, mean);
-        if (t == 0) {
-            const float nm = sqrtf(mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2]);
-            if (nm > 0.f) {
-                R[0][0] = mean[0] / nm, R[1][0] = mean[1] / nm, R[2][0] = mean[2] / nm;
+        // primary direction (w = 0 pads a thread's unused slots)
+        float g[SR_SLOTS][3], sw[SR_SLOTS];
+#pragma unroll
+        for (int j = 0; j < SR_SLOTS; ++j) {
+            const int i = t + j * SR_THREADS;
+            if (i < SR_SAMPLES) {
+                const float4 u = smp[i];
+                gradient_at<S>(L, K.ix, K.iy, K.iz, r * u.x, r * u.y, r * u.z, g[j]);
+                sw[j] = u.w;
             } else {
-                R[0][0] = 1.f, R[1][0] = 0.f, R[2][0] = 0.f;
+                g[j][0] = g[j][1] = g[j][2] = 0.f;
+                sw[j] = 0.f;
             }
         }
-        __syncthreads();
-        const float e1x = R[0][0], e1y = R[1][0], e1z = R[2][0];
-        // secondary direction from the parts perpendicular to e1
-        for (int i = t; i < ns; i += SR_THREADS) {
-            const float d = sg[i][0] * e1x + sg[i][1] * e1y + sg[i][2] * e1z;
-            sg[i][0] -= d * e1x;
-            sg[i][1] -= d * e1y;
-            sg[i][2] -= d * e1z;
-            sb[i] = nearest_direction(a.ico, sg[i]);
+        direction_peak(ico, g, sw, red, hist, mean);
+        float e1x, e1y, e1z;
+        {
+            const float nm = sqrtf(mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2]);
+            if (nm > 0.f) e1x = mean[0] / nm, e1y = mean[1] / nm, e1z = mean[2] / nm;
+            else e1x = 1.f, e1y = 0.f, e1z = 0.f;
         }
-        __syncthreads();
-        direction_peak(ns, sg, sw, sb, hist, mean);
+        // secondary direction from the parts perpendicular to e1
+#pragma unroll
+        for (int j = 0; j < SR_SLOTS; ++j) {
+            const float d = g[j][0] * e1x + g[j][1] * e1y + g[j][2] * e1z;
+            g[j][0] -= d * e1x;
+            g[j][1] -= d * e1y;
+            g[j][2] -= d * e1z;
+        }
+        direction_peak(ico, g, sw, red, hist, mean);
         if (t == 0) {
             float m0 = mean[0], m1 = mean[1], m2 = mean[2];
             const float d = m0 * e1x + m1 * e1y + m2 * e1z;
@@ -249,6 +273,7 @@ __global__ void __launch_bounds__(SR_THREADS) siftrank_kernel(const SiftRankArgs
                 m0 = px ? 0.f : -e1z, m1 = px ? e1z : 0.f, m2 = px ? -e1y : e1x;
                 nm = sqrtf(m0 * m0 + m1 * m1 + m2 * m2);
             }
+            R[0][0] = e1x, R[1][0] = e1y, R[2][0] = e1z;
             R[0][1] = m0 / nm, R[1][1] = m1 / nm, R[2][1] = m2 / nm;
             R[0][2] = e1y * R[2][1] - e1z * R[1][1];
             R[1][2] = e1z * R[0][1] - e1x * R[2][1];
@@ -256,32 +281,35 @@ __global__ void __launch_bounds__(SR_THREADS) siftrank_kernel(const SiftRankArgs
         }
         __syncthreads();
         // descriptor: samples at c + R u, gradients in the keypoint frame
-        for (int i = t; i < ns; i += SR_THREADS) {
-            const float ux = r * su[i][0], uy = r * su[i][1], uz = r * su[i][2];
+#pragma unroll
+        for (int j = 0; j < SR_SLOTS; ++j) {
+            const int i = t + j * SR_THREADS;
+            if (i >= SR_SAMPLES) continue;
+            const float4 u = smp[i];
+            const float ux = r * u.x, uy = r * u.y, uz = r * u.z;
             const float tx = R[0][0] * ux + R[0][1] * uy + R[0][2] * uz;
             const float ty = R[1][0] * ux + R[1][1] * uy + R[1][2] * uz;
             const float tz = R[2][0] * ux + R[2][1] * uy + R[2][2] * uz;
-            float g[3];
-            gradient_at<S>(L, K.ix, K.iy, K.iz, tx, ty, tz, g);
-            const float gx = R[0][0] * g[0] + R[1][0] * g[1] + R[2][0] * g[2];
-            const float gy = R[0][1] * g[0] + R[1][1] * g[1] + R[2][1] * g[2];
-            const float gz = R[0][2] * g[0] + R[1][2] * g[1] + R[2][2] * g[2];
-            const int spatial = (su[i][0] >= 0.f) + 2 * (su[i][1] >= 0.f) + 4 * (su[i][2] >= 0.f);
-            const int orient = (gx >= 0.f) + 2 * (gy >= 0.f) + 4 * (gz >= 0.f);
-            sb[i] = 8 * spatial + orient;
-            sg[i][0] = sw[i] * sqrtf(gx * gx + gy * gy + gz * gz);
+            float q[3];
+            gradient_at<S>(L, K.ix, K.iy, K.iz, tx, ty, tz, q);
+            const float gx = R[0][0] * q[0] + R[1][0] * q[1] + R[2][0] * q[2];
+            const float gy = R[0][1] * q[0] + R[1][1] * q[1] + R[2][1] * q[2];
+            const float gz = R[0][2] * q[0] + R[1][2] * q[1] + R[2][2] * q[2];
+            sbin[i] = (gx >= 0.f) + 2 * (gy >= 0.f) + 4 * (gz >= 0.f);
+            sval[i] = u.w * sqrtf(gx * gx + gy * gy + gz * gz);
         }
         __syncthreads();
-        if (t < 64) {
+        if (t < 64) {   // element 8 * spatial octant + orientation octant
+            const int o = t >> 3, ob = t & 7;
             float h = 0.f;
-            for (int i = 0; i < ns; ++i)
-                if (sb[i] == t) h += sg[i][0];
+            for (int i = oct[o]; i < oct[o + 1]; ++i) h += sbin[i] == ob ? sval[i] : 0.f;
             hist[t] = h;
         }
         __syncthreads();
         if (t < 64) {
             const float v = hist[t];
             int rank = 0;
+#pragma unroll 8
             for (int j = 0; j < 64; ++j) rank += (hist[j] < v) || (hist[j] == v && j < t);
             a.desc[(int64_t)kp * 64 + t] = (uint8_t)rank;
         }
@@ -321,6 +349,29 @@ LaunchSpec describe_spec(int storage, const DescribeArgs&, int n_max) {
 int enqueue_siftrank(int storage, const DescribeArgs& d, const sift3d_keypoint* kps, int n, const int* n_dev,
                      int n_cap, uint8_t* desc, float* rot, cudaStream_t st) {
     SiftRankArgs a{};
+    {   // the 8^3 cell centres of [-1, 1]^3 inside the unit ball, weight
+        // exp(-|u|^2 / (2 (1/2)^2)) (offsets and weight in units of r = 3 sigma),
+        // grouped by spatial octant and in z, y, x order within each
+        int k = 0;
+        for (int o = 0; o < 8; ++o) {
+            a.oct_start[o] = k;
+            for (int z = 0; z < 8; ++z)
+                for (int y = 0; y < 8; ++y)
+                    for (int x = 0; x < 8; ++x) {
+                        const float ux = ((x + 0.5f) / 8.f) * 2.f - 1.f, uy = ((y + 0.5f) / 8.f) * 2.f - 1.f;
+                        const float uz = ((z + 0.5f) / 8.f) * 2.f - 1.f;
+                        const float q = ux * ux + uy * uy + uz * uz;
+                        const int oct = (ux >= 0.f) + 2 * (uy >= 0.f) + 4 * (uz >= 0.f);
+                        if (q <= 1.f && oct == o && k < SR_SAMPLES) {
+                            a.smp[k][0] = ux, a.smp[k][1] = uy, a.smp[k][2] = uz;
+                            a.smp[k][3] = (float)std::exp(-(double)q / (2.0 * 0.25));
+                            ++k;
+                        }
+                    }
+        }
+        a.oct_start[8] = k;
+        if (k != SR_SAMPLES) return SIFT3D_EINVAL;
+    }
     {   // cyclic permutations of (0, +-1, +-phi), normalised
         const double phi = (1.0 + std::sqrt(5.0)) / 2.0, inv = 1.0 / std::sqrt(1.0 + phi * phi);
         int k = 0;

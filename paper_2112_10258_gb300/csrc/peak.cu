@@ -366,8 +366,12 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
 // ---- canonical order ------------------------------------------------------
 // Rank sort: the key of record i packs (octave, scale, iz, iy, ix, i), so keys
 // are unique and record i's place is the number of smaller keys.  Each CTA
-// ranks 128 records against all keys, read through shared memory in tiles.
-constexpr int SORT_THREADS = 128;
+// ranks 128 records against all keys, read through shared memory in tiles that
+// all 1024 threads stage at once; the 8 consecutive lanes of a record each count
+// every 8th key and add their counts.
+constexpr int SORT_RECORDS = 128;
+constexpr int SORT_LANES = 8;
+constexpr int SORT_THREADS = SORT_RECORDS * SORT_LANES;
 constexpr int SORT_TILE = kSortSmemKeys;
 
 __device__ __forceinline__ unsigned long long sort_key(const sift3d_keypoint& k, int idx) {
@@ -382,8 +386,9 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
     const int total = *a.count;
     const int n = min(total, a.capacity);
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = (a.tail_err != nullptr && *a.tail_err != 0) ? -2 : total;
-    if ((int)blockIdx.x * SORT_THREADS >= n) return;
-    const int i = blockIdx.x * SORT_THREADS + threadIdx.x;
+    if ((int)blockIdx.x * SORT_RECORDS >= n) return;
+    const int sub = threadIdx.x % SORT_LANES;
+    const int i = blockIdx.x * SORT_RECORDS + threadIdx.x / SORT_LANES;
     const unsigned long long mine = i < n ? sort_key(a.staging[i], i) : ~0ull;
     int rank = 0;
     for (int base = 0; base < n; base += SORT_TILE) {
@@ -391,9 +396,12 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
         __syncthreads();
         for (int j = threadIdx.x; j < len; j += SORT_THREADS) skeys[j] = sort_key(a.staging[base + j], base + j);
         __syncthreads();
-        for (int j = 0; j < len; ++j) rank += skeys[j] < mine;
+#pragma unroll 4
+        for (int j = sub; j < len; j += SORT_LANES) rank += skeys[j] < mine;
     }
-    if (i < n) a.out[rank] = a.staging[i];
+#pragma unroll
+    for (int off = 1; off < SORT_LANES; off <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, off);
+    if (i < n && sub == 0) a.out[rank] = a.staging[i];
 }
 
 template <typename S>
@@ -461,7 +469,7 @@ LaunchSpec peak_spec(int storage, const PeakTmaArgs& A) {
 LaunchSpec sort_spec(const SortArgs& a) {
     LaunchSpec s;
     s.func = reinterpret_cast<const void*>(&sort_kernel);
-    s.grid = dim3((unsigned)std::max(1, (a.capacity + SORT_THREADS - 1) / SORT_THREADS));
+    s.grid = dim3((unsigned)std::max(1, (a.capacity + SORT_RECORDS - 1) / SORT_RECORDS));
     s.block = dim3(SORT_THREADS);
     s.smem = 0;
     s.name = "sort";
