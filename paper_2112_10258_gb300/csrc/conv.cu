@@ -251,13 +251,31 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
     // y pass
     const int pairs = (nx + 1) / 2;
     if (tid < 2 * pairs) {
-        const int p = tid % pairs, h = tid / pairs;
+        const int h = tid >= pairs ? 1 : 0, p = tid - h * pairs;
         const int c = 2 * p, r0 = h * RY;
         const bool full = c + 1 < nx;
+        const int gy0 = y0 + r0 - R;   // first source row
         float2 v[RY + 2 * R];
+        bool walked = false;
+        if constexpr (MODE == 0) {
+            if (gy0 >= 0 && gy0 + RY + 2 * R <= a.ny) {
+                // rows inside the plane: walk them without clamps (pitch in pairs)
+                using PT = typename Pair<Tin>::T;
+                const PT* q = reinterpret_cast<const PT*>(src + (int64_t)z * a.src_pz + (int64_t)gy0 * a.src_py + c);
+                const int64_t step = a.src_py / 2;
 #pragma unroll
-        for (int t = 0; t < RY + 2 * R; ++t)
-            v[t] = load_src_pair<MODE, Tin>(a, src, z, min(max(y0 + r0 - R + t, 0), a.ny - 1), c, full);
+                for (int t = 0; t < RY + 2 * R; ++t) {
+                    v[t] = Pair<Tin>::get(*q);
+                    q += step;
+                }
+                walked = true;
+            }
+        }
+        if (!walked) {
+#pragma unroll
+            for (int t = 0; t < RY + 2 * R; ++t)
+                v[t] = load_src_pair<MODE, Tin>(a, src, z, min(max(gy0 + t, 0), a.ny - 1), c, full);
+        }
         if constexpr (MODE == 2) {   // this CTA's own rows of the sub-sampled level are G_0
             using PB = Pair<Tbase>;
 #pragma unroll
@@ -296,13 +314,13 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
         const int right = W - (RA + nx);
         const int per_line = RA + right;
         const int nb = RB > 0 ? 2 : 1;
-        for (int i = tid; i < nb * (ROW_TY / 2) * per_line; i += blockDim.x) {
-            const int bsel = i / ((ROW_TY / 2) * per_line);
-            const int rem = i - bsel * (ROW_TY / 2) * per_line;
-            const int rp = rem / per_line, e = rem - rp * per_line;
-            float2* line = (bsel == 0 ? mid : mid2) + rp * W;
-            if (e < RA) line[e] = line[RA];
-            else line[RA + nx + (e - RA)] = line[RA + nx - 1];
+        const int lane = tid & 31, nwarps = blockDim.x >> 5;   // blockDim.x is a multiple of 32
+        for (int l = tid >> 5; l < nb * (ROW_TY / 2); l += nwarps) {   // a warp per line
+            float2* line = (l < ROW_TY / 2 ? mid : mid2) + (l % (ROW_TY / 2)) * W;
+            for (int e = lane; e < per_line; e += 32) {
+                if (e < RA) line[e] = line[RA];
+                else line[RA + nx + (e - RA)] = line[RA + nx - 1];
+            }
         }
     }
     __syncthreads();
