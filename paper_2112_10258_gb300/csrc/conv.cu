@@ -65,10 +65,13 @@ __device__ __forceinline__ float2 f2(float w) { return make_float2(w, w); }
 template <int N, int R>
 __device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, int z0, int nz, bool interior,
                                               float2 (&v)[N]) {
-    if (interior) {
+    if (interior) {   // walk the planes
         const float2* p = src + (int64_t)(z0 - R) * pz2;
 #pragma unroll
-        for (int t = 0; t < N; ++t) v[t] = __ldg(p + t * pz2);
+        for (int t = 0; t < N; ++t) {
+            v[t] = __ldg(p);
+            p += pz2;
+        }
     } else {
 #pragma unroll
         for (int t = 0; t < N; ++t) v[t] = __ldg(src + (int64_t)min(max(z0 - R + t, 0), nz - 1) * pz2);
@@ -92,34 +95,44 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
     float2 pv[Z_TZ];
     const PT* prev = static_cast<const PT*>(a.prev) + pair;
     if (with_dog) {
+        if (z0 + Z_TZ <= a.nz) {   // walk the planes
+            const PT* q = prev + (int64_t)z0 * pz2;
 #pragma unroll
-        for (int j = 0; j < Z_TZ; ++j) pv[j] = P::get(prev[(int64_t)min(z0 + j, a.nz - 1) * pz2]);
+            for (int j = 0; j < Z_TZ; ++j) {
+                pv[j] = P::get(*q);
+                q += pz2;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < Z_TZ; ++j) pv[j] = P::get(prev[(int64_t)min(z0 + j, a.nz - 1) * pz2]);
+        }
     }
-    PT* dst = static_cast<PT*>(a.dst) + pair;
-    PT* dog = static_cast<PT*>(a.dog) + pair;
+    PT* dst = static_cast<PT*>(a.dst) + pair + (int64_t)z0 * pz2;
+    PT* dog = static_cast<PT*>(a.dog) + pair + (int64_t)z0 * pz2;
 #pragma unroll
     for (int j = 0; j < Z_TZ; ++j) {
-        const int z = z0 + j;
-        if (z >= a.nz) break;
+        if (z0 + j >= a.nz) break;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(a.taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
-        const int64_t off = (int64_t)z * pz2;
-        dst[off] = P::put(acc);
-        if (with_dog) dog[off] = P::put(make_float2(pv[j].x - acc.x, pv[j].y - acc.y));
+        *dst = P::put(acc);
+        if (with_dog) *dog = P::put(make_float2(pv[j].x - acc.x, pv[j].y - acc.y));
+        dst += pz2;
+        dog += pz2;
     }
     if constexpr (RB > 0) {   // the fused descriptor pre-blur, after the level so registers are reused
         float2 u[Z_TZ + 2 * RB];
         load_z_window<Z_TZ + 2 * RB, RB>(reinterpret_cast<const float2*>(a.src2) + pair, pz2, z0, a.nz,
                                          z0 - RB >= 0 && z0 + Z_TZ + RB <= a.nz, u);
-        PT* dst2 = static_cast<PT*>(a.dst2) + pair;
+        PT* dst2 = static_cast<PT*>(a.dst2) + pair + (int64_t)z0 * pz2;
 #pragma unroll
         for (int j = 0; j < Z_TZ; ++j) {
             if (z0 + j >= a.nz) break;
             float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = -RB; k <= RB; ++k) acc2 = __ffma2_rn(f2(a.taps2.w[k < 0 ? -k : k]), u[j + RB + k], acc2);
-            dst2[(int64_t)(z0 + j) * pz2] = P::put(acc2);
+            *dst2 = P::put(acc2);
+            dst2 += pz2;
         }
     }
 }
@@ -178,6 +191,24 @@ __device__ __forceinline__ float sub_mean(const Tin* p, int64_t py, int64_t pz) 
     acc += load_f(p + pz + py);
     acc += load_f(p + pz + py + 1);
     return acc * 0.125f;
+}
+
+// Four consecutive values (8- or 16-byte aligned) as floats.
+template <typename T> __device__ __forceinline__ float4 load4(const T* p);
+template <> __device__ __forceinline__ float4 load4<float>(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <> __device__ __forceinline__ float4 load4<__half>(const __half* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <> __device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // Source values of columns (c, c+1) at row gy of plane z (MODE as above); the
@@ -267,6 +298,37 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
                 for (int t = 0; t < RY + 2 * R; ++t) {
                     v[t] = Pair<Tin>::get(*q);
                     q += step;
+                }
+                walked = true;
+            }
+        } else if constexpr (MODE == 1) {
+            if (gy0 >= 0 && gy0 + RY + 2 * R <= a.ny) {   // rows inside: walk them without clamps
+                const Tin* q = src + (int64_t)z * a.src_pz + (int64_t)gy0 * a.src_py + c;
+#pragma unroll
+                for (int t = 0; t < RY + 2 * R; ++t) {
+                    const float v0 = load_f(q) * a.src_scale;
+                    v[t] = make_float2(v0, full ? load_f(q + 1) * a.src_scale : v0);
+                    q += a.src_py;
+                }
+                walked = true;
+            }
+        } else {
+            if (full && gy0 >= 0 && gy0 + RY + 2 * R <= a.ny) {
+                // rows inside, both columns inside: the four source columns 2c..2c+3 of
+                // each of the 2x2 (row, plane) lines in one load each; the means are
+                // summed in the order of sub_mean
+                const Tin* q = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy0) * a.src_py + 2 * c;
+#pragma unroll
+                for (int t = 0; t < RY + 2 * R; ++t) {
+                    const float4 r00 = load4(q), r01 = load4(q + a.src_py);
+                    const float4 r10 = load4(q + a.src_pz), r11 = load4(q + a.src_pz + a.src_py);
+                    float m0 = 0.f, m1 = 0.f;
+                    m0 += r00.x; m0 += r00.y; m0 += r01.x; m0 += r01.y;
+                    m0 += r10.x; m0 += r10.y; m0 += r11.x; m0 += r11.y;
+                    m1 += r00.z; m1 += r00.w; m1 += r01.z; m1 += r01.w;
+                    m1 += r10.z; m1 += r10.w; m1 += r11.z; m1 += r11.w;
+                    v[t] = make_float2(m0 * 0.125f, m1 * 0.125f);
+                    q += 2 * a.src_py;
                 }
                 walked = true;
             }
