@@ -189,7 +189,7 @@ def cpu_baseline(vol):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("conv.cu", "conv_tile.cuh", "peak.cu", "tma.cuh", "describe.cu", "common.cuh"):
+    for f in ("peak.cu", "tma.cuh", "common.cuh"):   # the sources of the dominant (peak) kernel
         with open(os.path.join(ROOT, "paper_2112_10258_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

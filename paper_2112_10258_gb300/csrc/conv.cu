@@ -193,24 +193,6 @@ __device__ __forceinline__ float sub_mean(const Tin* p, int64_t py, int64_t pz) 
     return acc * 0.125f;
 }
 
-// Four consecutive values (8- or 16-byte aligned) as floats.
-template <typename T> __device__ __forceinline__ float4 load4(const T* p);
-template <> __device__ __forceinline__ float4 load4<float>(const float* p) {
-    return __ldg(reinterpret_cast<const float4*>(p));
-}
-template <> __device__ __forceinline__ float4 load4<__half>(const __half* p) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-template <> __device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16* p) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-
 // Source values of columns (c, c+1) at row gy of plane z (MODE as above); the
 // second column repeats the first when c+1 is beyond the row (odd nx).
 template <int MODE, typename Tin>
@@ -309,26 +291,6 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
                     const float v0 = load_f(q) * a.src_scale;
                     v[t] = make_float2(v0, full ? load_f(q + 1) * a.src_scale : v0);
                     q += a.src_py;
-                }
-                walked = true;
-            }
-        } else {
-            if (full && gy0 >= 0 && gy0 + RY + 2 * R <= a.ny) {
-                // rows inside, both columns inside: the four source columns 2c..2c+3 of
-                // each of the 2x2 (row, plane) lines in one load each; the means are
-                // summed in the order of sub_mean
-                const Tin* q = src + (int64_t)(2 * z) * a.src_pz + (int64_t)(2 * gy0) * a.src_py + 2 * c;
-#pragma unroll
-                for (int t = 0; t < RY + 2 * R; ++t) {
-                    const float4 r00 = load4(q), r01 = load4(q + a.src_py);
-                    const float4 r10 = load4(q + a.src_pz), r11 = load4(q + a.src_pz + a.src_py);
-                    float m0 = 0.f, m1 = 0.f;
-                    m0 += r00.x; m0 += r00.y; m0 += r01.x; m0 += r01.y;
-                    m0 += r10.x; m0 += r10.y; m0 += r11.x; m0 += r11.y;
-                    m1 += r00.z; m1 += r00.w; m1 += r01.z; m1 += r01.w;
-                    m1 += r10.z; m1 += r10.w; m1 += r11.z; m1 += r11.w;
-                    v[t] = make_float2(m0 * 0.125f, m1 * 0.125f);
-                    q += 2 * a.src_py;
                 }
                 walked = true;
             }
