@@ -195,11 +195,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(label):
+def measured_traffic(label, storage):
+    """DRAM bytes per launch of the dominant kernel from the stored ncu capture,
+    or None when the capture is of another kernel, storage type or source."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
-        if t.get("source_hash") == kernel_source_hash() and t.get("label") == label:
+        if (t.get("source_hash") == kernel_source_hash() and t.get("label") == label
+                and t.get("storage") == storage):
             return float(t["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -608,7 +611,7 @@ def main():
     tot = sum(r[1] for r in breakdown)
     dom_label, dom_ms, dom_bytes = breakdown[0]
     dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = measured_traffic(dom_label)
+    traffic = measured_traffic(dom_label, args.storage)
     roofline = {"bound": "hbm", "kernel": dom_label, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                 "frac": dom_gbs / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": dom_bytes, "mean_ms": dom_ms}
