@@ -140,13 +140,15 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
 // ---- y/x pass of full rows (nx <= 256) with paired FP32 FMAs -----------------
 // One CTA filters rows y0 .. y0+15 of one plane, full width.
 //   y pass: a task owns a column pair and 8 output rows; it loads the 8 + 2R
-//           source rows (clamped y) into registers and filters both columns at
-//           once with __ffma2_rn.  Results go to shared memory as row pairs:
+//           source rows (clamped y; a task whose rows all lie inside the plane
+//           walks a row pointer instead) into registers and filters both
+//           columns at once with __ffma2_rn.  Results go to shared memory as row pairs:
 //           element [rp][c] holds (row 2rp, row 2rp+1) of column c, so the x
 //           pass reads two rows with one 8-byte access.
 //   aprons: each row-pair line carries RA = R + (R & 1) copies of column 0 on
 //           the left and copies of column nx-1 on the right, which is the
-//           clamp-to-edge border: the x pass reads without index clamps.
+//           clamp-to-edge border: the x pass reads without index clamps.  A
+//           warp fills one line at a time, lanes along it.
 //   x pass: a task owns a row pair and 8 output columns; it reads its window
 //           with 16-byte shared loads and filters both rows at once.
 // Per column and row every output is the scalar chain fmaf(w_|k|, in, acc) in
