@@ -603,6 +603,30 @@ def test_icosahedron_directions():
     assert np.all(np.sum(np.abs(D - 1 / np.sqrt(5)) < 1e-12, axis=1) == 5)   # five nearest neighbours each
 
 
+def test_siftrank_samples_exact_enumeration():
+    # cell centre i of the 8-cell axis is u = (2i - 7) / 8 in units of r, so it
+    # lies in the ball |u| <= 1 iff sum (2i - 7)^2 <= 64: an integer count
+    cells = [(i, j, k) for k in range(8) for j in range(8) for i in range(8)
+             if (2 * i - 7) ** 2 + (2 * j - 7) ** 2 + (2 * k - 7) ** 2 <= 64]
+    sigma = 1.7
+    r = 3.0 * sigma
+    u, w = O.siftrank_samples(sigma)
+    assert len(cells) == u.shape[0] == w.shape[0] == 280
+    expect = np.array([[(2 * i - 7) / 8.0, (2 * j - 7) / 8.0, (2 * k - 7) / 8.0] for i, j, k in cells]) * r
+    np.testing.assert_allclose(u, expect, rtol=0, atol=1e-12)          # same points, same (z, y, x) order
+    q = np.array([(2 * i - 7) ** 2 + (2 * j - 7) ** 2 + (2 * k - 7) ** 2 for i, j, k in cells]) / 64.0
+    np.testing.assert_allclose(w, np.exp(-q / (2 * 0.5 ** 2)), rtol=1e-14)   # exp(-|u|^2 / (2 (r/2)^2))
+    # every spatial octant (sign pattern) holds 35 samples, and each axis
+    # reflection maps the set onto itself
+    octant = (u[:, 0] >= 0) + 2 * (u[:, 1] >= 0) + 4 * (u[:, 2] >= 0)
+    assert np.bincount(octant, minlength=8).tolist() == [35] * 8
+    key = {tuple(np.round(p / r * 8).astype(int)) for p in u}
+    for axis in range(3):
+        flip = np.ones(3)
+        flip[axis] = -1
+        assert {tuple(np.round(p * flip / r * 8).astype(int)) for p in u} == key
+
+
 def _analytic_volume(fn, shape=(40, 40, 40)):
     z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
     return fn(x, y, z)
