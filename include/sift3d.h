@@ -279,11 +279,13 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
                          double sigma, float* dev_out, void* stream);
 
 /* The same blur for callers that cannot allocate device memory: code that runs
- * where cudaMalloc is unavailable or not allowed (inside a host callback, in an
- * allocator's own reclaim path, in a loop that must never enter the allocator)
- * or that is handed only its input and output buffers.  This call allocates
- * nothing, needs no context, and takes trunc explicitly (4.0 matches the
- * default params).  No counterpart in the paper.
+ * where cudaMalloc is unavailable or not allowed (in an allocator's own reclaim
+ * path, in a loop that must never enter the allocator) or that is handed only
+ * its input and output buffers.  This call allocates nothing, needs no context,
+ * and takes trunc explicitly (4.0 matches the default params).  It launches
+ * kernels and, on its first call on a device, looks up a symbol address, so it
+ * must not be called from a host function or callback running on a CUDA stream
+ * (CUDA forbids CUDA calls there).  No counterpart in the paper.
  *   Scratch: one library-owned device array of 2 * SIFT3D_BLUR_NOALLOC_MAX_ELEMS
  *   floats (32 MiB) that every GPU loading the library holds until the process
  *   exits.  A volume fits when roundup(nx, 8) * ny * nz <= the maximum (a

@@ -32,7 +32,7 @@ blocking or fusion:
 * Sub-voxel refinement (one Newton step on the 4D DoG quadratic): not in the
   paper.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 
 * sigma0 = 1.6, sigma_in = 0.5, S = 3 scales per octave, S + 3 = 6 Gaussian levels
   with sigma_s = sigma0 * 2^(s/S); octave 0 starts with a blur of

@@ -1,8 +1,10 @@
 // sift3d_gaussian_blur_noalloc: the separable 3D Gaussian blur for callers that
 // cannot allocate device memory themselves - code running where cudaMalloc is
-// unavailable or forbidden (a host callback, a custom allocator's own reclaim
-// path, a real-time loop that must not touch the allocator, or an embedding
-// that hands the library only its input and output buffers).
+// unavailable or forbidden (a custom allocator's own reclaim path, a real-time
+// loop that must not touch the allocator, or an embedding that hands the
+// library only its input and output buffers).  It makes CUDA calls (kernel
+// launches; a symbol lookup on the first call per device), so it cannot run
+// inside a host function or callback enqueued on a stream.
 //
 // The two float32 intermediate volumes live in one file-scope device array that
 // every GPU which loads this library holds until the process exits.  Host code

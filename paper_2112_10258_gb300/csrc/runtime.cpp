@@ -15,7 +15,14 @@ namespace {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int radius_of(double sigma, double trunc) { return (int)std::ceil(trunc * sigma); }
+// ceil(trunc * sigma), or kMaxRadius + 1 for any sigma or trunc that is not a
+// positive finite number with trunc * sigma <= kMaxRadius (checked before the
+// conversion to int, which is undefined for NaN or out-of-range values).
+int radius_of(double sigma, double trunc) {
+    const double r = trunc * sigma;
+    if (!(sigma > 0.0) || !(trunc > 0.0) || !(r <= (double)kMaxRadius)) return kMaxRadius + 1;
+    return (int)std::ceil(r);
+}
 
 }  // namespace
 
@@ -46,8 +53,8 @@ int fail(std::string* err, const char* msg) {
 }  // namespace
 
 int validate_params(const sift3d_params& p, std::string* err) {
-    if (!(p.sigma0 > 0.0) || !(p.sigma_in >= 0.0) || !(p.sigma0 > p.sigma_in))
-        return fail(err, "need sigma0 > sigma_in >= 0");
+    if (!(p.sigma0 > 0.0) || !(p.sigma_in >= 0.0) || !(p.sigma0 > p.sigma_in) || !std::isfinite(p.sigma0))
+        return fail(err, "need finite sigma0 > sigma_in >= 0");
     if (p.scales_per_octave < 1 || p.scales_per_octave > SIFT3D_MAX_SCALES)
         return fail(err, "scales_per_octave must be in 1..5");
     if (p.border < 1) return fail(err, "border must be >= 1");

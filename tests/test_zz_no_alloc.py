@@ -21,12 +21,18 @@ def S():
 
 
 def test_noalloc_blur_matches_context_blur_twice(S):
+    """Small volume, then the 145x174x145 volume, then the small one again: the
+    third call runs in scratch that the large call filled with finite data, and
+    the small volume's row padding differs from the large one's, so an element
+    read before it is written would show as a difference.  Both runs use the
+    same kernels as the context blur, so every output must equal it bit for bit."""
     from paper_2112_10258_gb300 import capi
     from workloads.volumes import blob_volume, brain_like_volume
     det = S.Sift3D()
     stream = torch.cuda.current_stream().cuda_stream
-    cases = [(brain_like_volume(seed=4), 2.4525), (blob_volume(seed=9, shape=(37, 29, 23)), 1.2263)]
-    for vol, sigma in cases:
+    small = (blob_volume(seed=9, shape=(37, 29, 23)), 1.2263)
+    large = (brain_like_volume(seed=4), 2.4525)
+    for vol, sigma in (small, large, small):
         d = torch.from_numpy(vol).cuda()
         nz, ny, nx = vol.shape
         ref = det.gaussian_blur(d, sigma)
@@ -36,7 +42,7 @@ def test_noalloc_blur_matches_context_blur_twice(S):
         torch.cuda.synchronize()
         r, o = ref.cpu().numpy(), out.cpu().numpy()
         assert np.all(np.isfinite(o))
-        assert np.max(np.abs(o - r)) <= 1e-5 * np.max(np.abs(r))
+        assert np.array_equal(o, r), f"max difference {np.max(np.abs(o - r))} on {vol.shape}"
     det.close()
 
 
