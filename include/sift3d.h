@@ -121,12 +121,6 @@ typedef struct sift3d_params {
     uint64_t hbm_budget_bytes;   /* serving admission budget (0 = 40 GiB)      */
     int32_t  max_keypoints;      /* serving: keypoints kept per request (8192) */
     int32_t  max_inflight;       /* serving: requests on the device at once (4) */
-    int32_t  fuse_small_octaves; /* 0 (default) = one launch per pass; 1 =
-                                    the last octaves of at most 32768 voxels
-                                    whose z-slabs fit the shared memory of a
-                                    thread-block cluster build their pyramids
-                                    in one cluster launch (bitwise the same
-                                    results; measured slower on GB300)       */
     int32_t  refine;             /* 0 (default); 1 = one Newton step on the
                                     4D (x, y, z, scale) quadratic of the DoG
                                     through the keypoint's 3^4 neighbourhood
@@ -134,9 +128,16 @@ typedef struct sift3d_params {
                                     dog report the interpolated extremum.  No
                                     counterpart in the paper; the keypoint set
                                     does not change.                          */
-    int32_t  use_pdl;            /* 0 (default); 1 = chain the detect graph's
-                                    kernels with programmatic dependent launch;
-                                    2 = only between kernels of octaves >= 1 */
+    int32_t  test_wait_timeout;  /* 0 (default).  k > 0 = for testing the error
+                                    path: the first k detects of this context
+                                    make the first wait of every peak-kernel
+                                    CTA for its staged planes one non-blocking
+                                    test, which finds the copy still in
+                                    flight; the CTA sets the error flag, waits
+                                    for all of its copies to land and leaves,
+                                    and sift3d_detect returns
+                                    SIFT3D_ETIMEDOUT.  Later detects on the
+                                    same context run normally.  0..1000.     */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

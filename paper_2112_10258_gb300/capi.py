@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("desc_method", C.c_int32),
         ("pattern_seed", C.c_uint64), ("storage", C.c_int32), ("use_graphs", C.c_int32),
         ("hbm_budget_bytes", C.c_uint64), ("max_keypoints", C.c_int32), ("max_inflight", C.c_int32),
-        ("fuse_small_octaves", C.c_int32), ("refine", C.c_int32), ("use_pdl", C.c_int32),
+        ("refine", C.c_int32), ("test_wait_timeout", C.c_int32),
     ]
 
 

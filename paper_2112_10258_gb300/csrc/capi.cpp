@@ -54,6 +54,8 @@ struct sift3d_ctx {
     int64_t blur_scratch_elems = 0;    // per volume
     char* arena = nullptr;             // device memory every cached shape's pyramid uses
     size_t arena_bytes = 0;
+    int test_timeouts_left = 0;        // detects still to run with the peak wait test
+    int* test_flag = nullptr;          // device int read by the peak kernel (test_wait_timeout > 0)
 };
 
 namespace {
@@ -102,6 +104,7 @@ int get_entry(sift3d_ctx* c, int nx, int ny, int nz, int dtype, int capacity, De
         auto ent = std::make_unique<DetectEntry>();
         rc = bind_workspace(pl, capacity, c->arena, &ent->ws, &err);
         if (rc != SIFT3D_OK) return set_err(c, rc, err);
+        ent->ws.test_flag = c->test_flag;
         it = c->cache.emplace(key, std::move(ent)).first;
     }
     DetectEntry* e = it->second.get();
@@ -441,8 +444,7 @@ int sift3d_default_params(sift3d_params* out) {
     out->hbm_budget_bytes = 40ull << 30;
     out->max_keypoints = 8192;
     out->max_inflight = 4;
-    out->fuse_small_octaves = 0;
-    out->use_pdl = 0;
+    out->test_wait_timeout = 0;
     out->refine = 0;
     return SIFT3D_OK;
 }
@@ -472,6 +474,7 @@ int sift3d_create(const sift3d_params* params, sift3d_ctx** out) {
     auto* c = new (std::nothrow) sift3d_ctx();
     if (!c) return SIFT3D_ENOMEM;
     c->p = *params;
+    c->test_timeouts_left = params->test_wait_timeout;
     make_pattern(c->p, c->pattern);
     *out = c;
     return SIFT3D_OK;
@@ -485,6 +488,7 @@ void sift3d_destroy(sift3d_ctx* ctx) {
     ctx->cache.clear();
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
+    if (ctx->test_flag) cudaFree(ctx->test_flag);
     delete ctx;
 }
 
@@ -501,11 +505,26 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
         return set_err(ctx, SIFT3D_EINVAL, "each dimension must be in 1..4095");
     int rc = ensure_device(ctx);
     if (rc != SIFT3D_OK) return rc;
+    if (ctx->p.test_wait_timeout > 0 && ctx->test_flag == nullptr) {
+        if (cudaMalloc(&ctx->test_flag, sizeof(int)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ctx->test_flag = nullptr;
+            return set_err(ctx, SIFT3D_ENOMEM, "test flag allocation");
+        }
+        ctx->cache.clear();   // cached graphs were built without the flag
+        ctx->last = nullptr;
+    }
     DetectEntry* ent = nullptr;
     rc = get_entry(ctx, nx, ny, nz, dtype, capacity, &ent);
     if (rc != SIFT3D_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::string err;
+    if (ctx->test_flag != nullptr) {   // testing the timeout path: set or clear the device flag
+        const int flag = ctx->test_timeouts_left > 0 ? 1 : 0;
+        if (ctx->test_timeouts_left > 0) --ctx->test_timeouts_left;
+        if (cudaMemsetAsync(ctx->test_flag, flag, sizeof(int), st) != cudaSuccess)
+            return set_err(ctx, SIFT3D_ECUDA, "test flag");
+    }
     rc = enqueue_detect(ent, dev_vol, dtype, dev_out, ctx->p.use_graphs != 0, st, &err);
     if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
     ctx->last = ent;
@@ -515,7 +534,7 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
         cudaError_t e = cudaMemcpyAsync(&h, ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("detect: ") + cudaGetErrorString(e));
-        if (h == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "a bounded device wait ran out (octave-tail barrier or peak tile load)");
+        if (h == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "a bounded device wait ran out (peak kernel plane copy)");
         *n_out = h;
         if (h > capacity) return set_err(ctx, SIFT3D_ECAPACITY, "more keypoints than capacity");
     }

@@ -32,14 +32,6 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(flo
     return __float2bfloat16_rn(v);
 }
 
-// Programmatic dependent launch: a kernel lets its dependents start launching
-// (they are scheduled once every CTA of this grid has started) and waits for
-// its own predecessors' completion and memory before touching their outputs.
-// Both are no-ops for a kernel that was not launched as a programmatic
-// dependent.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // Taps of a symmetric 1D Gaussian: w[0] is the centre, w[k] the weight at +-k.
 struct Taps {
     float w[kMaxRadius + 1];
@@ -68,7 +60,7 @@ struct ConvXYArgs {
 constexpr int kFusedBlurRadius = 4;
 
 // Per-detect device counters: [0] keypoints found, [1] total reported by the
-// sort (-2 = a tail-kernel barrier wait ran out), [2] tail barrier, [3] tail error.
+// sort (-2 = a bounded device wait ran out), [2] unused, [3] error flag.
 constexpr int kDetectCounters = 4;
 
 // ---- conv_z: z pass over columns, epilogue writes G_s and the DoG -------------
@@ -103,22 +95,23 @@ struct PeakArgs {
 // lie at a constant stride in the workspace and are described by one 4D tensor
 // map (x, y, z, level), passed as a __grid_constant__ kernel parameter.
 struct PeakTmaArgs {   // 128-byte aligned through CUtensorMap
-    CUtensorMap dogs;
+    CUtensorMap dogs;                   // box: a CTA's tile plus halo of one DoG level
     PeakArgs a;
     int x_start;                        // x of the first tile's halo origin (multiple of 8)
+    const int* test_flag;               // null, or *test_flag != 0: a CTA's first wait is one non-blocking test
     int* err;                           // set to 1 when a TMA wait runs out
 };
 
 // Tile geometry of the peak kernel for a storage type: the halo origin of the
-// first x tile and the TMA box (x, y, z) of one level.
-void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z);
+// first x tile and the TMA box (x, y, z, levels) of one copy.
+void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z, int* box_l);
 
 // ---- canonical sort of the staging records into the caller's array --------
 struct SortArgs {
     const sift3d_keypoint* staging;
     sift3d_keypoint* out;
     const int* count;
-    const int* tail_err;        // non-zero: the detect failed, report -2
+    const int* err;             // non-zero: a bounded wait ran out, report -2
     int* count_out;             // total detected (may exceed capacity)
     int capacity;
 };
@@ -161,33 +154,6 @@ struct ReadLevelArgs {
     float* dst;
 };
 
-// ---- small-octave kernel: the pyramids of the last octaves in one cluster ----
-constexpr int kTailCluster = 16;     // CTAs of the cluster where the device can hold it
-constexpr int kTailClusterPortable = 8;   // otherwise
-constexpr int kTailMaxSlab = 5;      // z planes per CTA (octave nz <= cluster * 5)
-
-struct TailOctave {
-    int nx, ny, nz;
-    int64_t py, pz;                         // level pitches (elements)
-    void* G[kMaxLevels];                    // G_0..G_{S+2} (storage type)
-    void* D[kMaxDogs];                      // D_0..D_{S+1}
-    void* B[SIFT3D_MAX_SCALES];             // pre-blurred G_1..G_S (when r_desc > 0)
-};
-
-struct TailArgs {
-    int n_oct;                              // octaves run by the kernel
-    int max_nz;                             // largest nz among them
-    int slab_planes;                        // planes per shared slab buffer: ceil(max_nz / cluster)
-    int L, S;                               // Gaussian levels and scales per octave
-    const void* src;                        // level S of the octave before the first one
-    int64_t src_py, src_pz;
-    int r_inc[kMaxLevels];                  // radius and taps of level s = index + 1
-    Taps t_inc[kMaxLevels];
-    int r_desc;                             // descriptor pre-blur (0 = none)
-    Taps t_desc;
-    TailOctave oct[SIFT3D_MAX_OCTAVES];
-};
-
 // A kernel launch with its single by-value argument struct, usable both for a
 // direct launch and as a CUDA graph kernel node.
 struct LaunchSpec {
@@ -195,10 +161,9 @@ struct LaunchSpec {
     dim3 grid, block;
     size_t smem = 0;
     const char* name = "";
-    int cluster = 0;          // > 0: thread-block cluster of this many CTAs along x
 };
 
-// Launch of a spec on a stream (cluster launches go through cudaLaunchKernelEx).
+// Launch of a spec on a stream.
 cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st);
 
 // Launch builders (one per kernel family).  `storage` is SIFT3D_STORAGE_*,
@@ -213,10 +178,5 @@ LaunchSpec match_spec(int kind, const MatchArgs& a);
 // SIFT-Rank descriptors of keypoints on the levels of d.lv (G_s, not pre-blurred).
 int enqueue_siftrank(int storage, const DescribeArgs& d, const sift3d_keypoint* kps, int n, const int* n_dev,
                      int n_cap, uint8_t* desc, float* rot, cudaStream_t st);
-LaunchSpec tail_spec(int storage, const TailArgs& a);
-int tail_cluster_size(int storage, const TailArgs& a);   // 16, 8, or 0 (cannot run)
-// Row pitch of the small-octave kernel's shared slabs (odd: conflict-free columns).
-__host__ __device__ constexpr int tail_row_pitch(int nx) { return nx | 1; }
-size_t tail_smem_bytes(int plane_elems, int slab_planes);   // dynamic shared memory of the small-octave kernel
 
 }  // namespace sift3d

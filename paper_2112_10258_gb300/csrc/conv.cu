@@ -30,8 +30,6 @@ using namespace conv_detail;
 template <int R, typename Tin, bool SUB, typename Tbase>
 __global__ void __launch_bounds__(XY_THREADS) conv_xy_kernel(const ConvXYArgs a) {
     extern __shared__ float sm[];
-    pdl_launch_dependents();
-    pdl_wait();
     conv_xy_tile<R, Tin, SUB, Tbase>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
@@ -80,8 +78,6 @@ __device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, in
 
 template <int R, typename S, int RB>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
-    pdl_launch_dependents();
-    pdl_wait();
     using P = Pair<S>;
     using PT = typename P::T;
     const int64_t pair = (int64_t)blockIdx.x * Z_THREADS + threadIdx.x;
@@ -250,8 +246,6 @@ template <int R, int MODE, typename Tin, typename Tbase, int RB>
 __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
     static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
     extern __shared__ __align__(16) float2 rows_sm[];
-    pdl_launch_dependents();
-    pdl_wait();
     const int nx = a.nx;
     const int W = row_line(nx, R);
     constexpr int RA = row_apron(R);

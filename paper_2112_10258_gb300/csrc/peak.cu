@@ -40,6 +40,7 @@ constexpr int TX = 32, TY = 8, TZ = 8;
 constexpr int THREADS = TX * TY;
 constexpr int SY = TY + 2, SZ = TZ + 2;
 constexpr int SURV = 512;                     // pass-2 list of one CTA
+constexpr int kDrainPolls = 1 << 26;          // wait for a copy still landing after a failed wait
 
 // Staged row width: the 34 voxels of a halo row rounded up so that the TMA box
 // row is a multiple of 16 bytes.
@@ -273,12 +274,30 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
     const int ys = a.border - 1 + blockIdx.y * TY;
     const int zs = a.border - 1 + blockIdx.z * TZ;
 
-    pdl_launch_dependents();
-    pdl_wait();     // the DoG levels are complete (no-op without a programmatic edge)
-    if (tid == 0) n_surv = 0;
-    const bool staged = tma::stage_tile(&bar, (unsigned)(NL * LV * sizeof(S)), A.err,
-                                        [&] { tma::load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar); });
-    if (!staged) return;   // error flag set; the whole CTA leaves together
+    if (tid == 0) {
+        n_surv = 0;
+        tma::mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        tma::mbar_expect_tx(&bar, (unsigned)(NL * LV * sizeof(S)));
+        tma::load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar);
+    }
+    // Bounded wait, CTA-uniform.  With the test flag it is a single non-blocking
+    // test, which finds the copy still in flight.  On a timeout the detect's
+    // error flag is set and thread 0 waits for the copy to land (a far longer
+    // bound) before the whole CTA leaves, so no copy reaches shared memory after
+    // the CTA's exit.
+    const bool first_test = A.test_flag != nullptr && *A.test_flag != 0;
+    const bool landed = first_test ? tma::mbar_test(&bar, 0) : tma::mbar_wait_bounded(&bar, 0, tma::kWaitPolls);
+    if (!__syncthreads_and(landed)) {
+        if (tid == 0) {
+            atomicExch(A.err, 1);
+            tma::mbar_wait_bounded(&bar, 0, kDrainPolls);
+        }
+        return;
+    }
 
     const int b = a.border;
     const int x = xs + 1 + lane, y = ys + 1 + w;
@@ -382,10 +401,9 @@ __device__ __forceinline__ unsigned long long sort_key(const sift3d_keypoint& k,
 
 __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
     __shared__ unsigned long long skeys[SORT_TILE];
-    pdl_wait();
     const int total = *a.count;
     const int n = min(total, a.capacity);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = (a.tail_err != nullptr && *a.tail_err != 0) ? -2 : total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = (a.err != nullptr && *a.err != 0) ? -2 : total;
     if ((int)blockIdx.x * SORT_RECORDS >= n) return;
     const int sub = threadIdx.x % SORT_LANES;
     const int i = blockIdx.x * SORT_RECORDS + threadIdx.x / SORT_LANES;
@@ -429,13 +447,14 @@ void peak_geometry(const PeakArgs& a, int* x_start, int* box_x, int* gx, size_t*
 
 }  // namespace
 
-void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z) {
+void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z, int* box_l) {
     int gx;
     size_t smem;
     if (storage == SIFT3D_STORAGE_F32) peak_geometry<float>(a, x_start, box_x, &gx, &smem);
     else peak_geometry<__half>(a, x_start, box_x, &gx, &smem);
     *box_y = SY;
     *box_z = SZ;
+    *box_l = a.n_scales + 2;   // every DoG level in one copy
 }
 
 LaunchSpec peak_spec(int storage, const PeakTmaArgs& A) {

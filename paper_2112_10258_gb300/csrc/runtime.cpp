@@ -72,9 +72,8 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.storage < SIFT3D_STORAGE_F32 || p.storage > SIFT3D_STORAGE_BF16) return fail(err, "bad storage");
     if (p.max_keypoints < 0 || p.max_keypoints > (1 << 20)) return fail(err, "max_keypoints must be in 0..2^20");
     if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
-    if (p.use_pdl < 0 || p.use_pdl > 2) return fail(err, "use_pdl must be 0, 1 or 2");
     if (p.refine < 0 || p.refine > 1) return fail(err, "refine must be 0 or 1");
-    if (p.fuse_small_octaves < 0 || p.fuse_small_octaves > 1) return fail(err, "fuse_small_octaves must be 0 or 1");
+    if (p.test_wait_timeout < 0 || p.test_wait_timeout > 1000) return fail(err, "test_wait_timeout must be in 0..1000");
 
     // filter radii of the schedule
     const int S = p.scales_per_octave;
@@ -133,22 +132,6 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
         cz /= 2;
     }
     if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
-    // The small-octave kernel takes the longest run of last octaves (from
-    // octave 1 on) of at most kTailMaxVoxels voxels whose z-slabs fit its
-    // shared memory: ceil(nz / 16) planes of each level per CTA.
-    pl.tail_start = pl.nO;
-    if (p.fuse_small_octaves)
-        for (int o = pl.nO - 1; o >= 1; --o) {
-            const OctaveGeom& g = pl.oct[o];
-            // slabs for the 16-CTA cluster; a device that cannot hold it makes
-            // the detect fall back to separate launches (build_detect)
-            const int slab = (g.nz + kTailCluster - 1) / kTailCluster;
-            const bool fits = slab <= kTailMaxSlab && g.voxels() <= kTailMaxVoxels &&
-                              tail_smem_bytes(tail_row_pitch(g.nx) * g.ny, slab) <= kTailMaxSmem;
-            if (!fits) break;
-            pl.tail_start = o;
-        }
-
     size_t off = 0;
     for (int o = 0; o < pl.nO; ++o) {
         const size_t lvl = round_up((size_t)(pl.oct[o].pz * pl.oct[o].nz) * pl.elem, 256);
@@ -341,56 +324,8 @@ void free_workspace(Workspace* ws) {
     ws->base = nullptr;
 }
 
-TailArgs make_tail_args(const Workspace& ws) {
-    const Plan& pl = ws.plan;
-    TailArgs a;
-    memset(&a, 0, sizeof(a));
-    a.n_oct = pl.nO - pl.tail_start;
-    a.L = pl.L;
-    a.S = pl.S;
-    const int prev = pl.tail_start - 1;
-    a.src = ws.G(prev, pl.S);
-    a.src_py = pl.oct[prev].py;
-    a.src_pz = pl.oct[prev].pz;
-    for (int s = 0; s + 1 < pl.L; ++s) {
-        a.r_inc[s] = pl.r_inc[s];
-        a.t_inc[s] = pl.t_inc[s];
-    }
-    a.r_desc = pl.r_desc;
-    a.t_desc = pl.t_desc;
-    for (int i = 0; i < a.n_oct; ++i) a.max_nz = std::max(a.max_nz, pl.oct[pl.tail_start + i].nz);
-    for (int i = 0; i < a.n_oct; ++i) {
-        const int o = pl.tail_start + i;
-        TailOctave& t = a.oct[i];
-        t.nx = pl.oct[o].nx;
-        t.ny = pl.oct[o].ny;
-        t.nz = pl.oct[o].nz;
-        t.py = pl.oct[o].py;
-        t.pz = pl.oct[o].pz;
-        for (int s = 0; s < pl.L; ++s) t.G[s] = ws.G(o, s);
-        for (int s = 0; s < pl.nD; ++s) t.D[s] = ws.D(o, s);
-        for (int s = 1; s <= pl.S; ++s) t.B[s - 1] = ws.B(o, s);
-    }
-    const int ncta = tail_cluster_size(pl.p.storage, a);
-    a.slab_planes = ncta > 0 ? (a.max_nz + ncta - 1) / ncta : 0;
-    return a;
-}
-
 cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st) {
-    if (s.cluster <= 0) return cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = s.grid;
-    cfg.blockDim = s.block;
-    cfg.dynamicSmemBytes = s.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr{};
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = (unsigned)s.cluster;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, s.func, args);
+    return cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
 }
 
 PeakArgs make_peak_args(const Workspace& ws, int o) {
@@ -451,8 +386,9 @@ bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
     memset(&A, 0, sizeof(A));
     A.a = make_peak_args(ws, o);
     A.err = ws.count + 3;
-    int box_x, box_y, box_z;
-    peak_layout(pl.p.storage, A.a, &A.x_start, &box_x, &box_y, &box_z);
+    int box_x, box_y, box_z, box_l;
+    peak_layout(pl.p.storage, A.a, &A.x_start, &box_x, &box_y, &box_z, &box_l);
+    A.test_flag = ws.test_flag;
     const size_t stride = pl.off_D[o][1] - pl.off_D[o][0];
     for (int s = 1; s + 1 < pl.nD; ++s)
         if (pl.off_D[o][s + 1] - pl.off_D[o][s] != stride) return false;
@@ -461,7 +397,7 @@ bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
     const CUtensorMapDataType dt = map_type(pl.p.storage);
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)pl.nD};
     const cuuint64_t strides[3] = {(cuuint64_t)g.py * pl.elem, (cuuint64_t)g.pz * pl.elem, (cuuint64_t)stride};
-    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)pl.nD};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)box_l};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = enc(&A.dogs, dt, 4, ws.D(o, 0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -495,15 +431,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
     bool fused[SIFT3D_MAX_OCTAVES][kMaxLevels] = {};
     *first_node = -1;
-    // the small-octave kernel runs when the device can hold its cluster;
-    // otherwise every octave takes the separate launches
-    TailArgs tail_args{};
-    int tail_start = pl.nO;
-    if (pl.tail_start < pl.nO) {
-        tail_args = make_tail_args(ws);
-        if (tail_args.slab_planes > 0) tail_start = pl.tail_start;
-    }
-    for (int o = 0; o < tail_start; ++o) {
+    for (int o = 0; o < pl.nO; ++o) {
         const OctaveGeom& g = pl.oct[o];
         int prev = -1;  // node that produced G_{s-1}
         for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
@@ -635,30 +563,9 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             }
         }
     }
-    if (tail_start < pl.nO) {
-        // the pyramids of the small octaves in one cluster launch, then their
-        // peak detection as ordinary launches
-        const int tn = add(tail_spec(st, tail_args), tail_args, {g_node[tail_start - 1][pl.S]});
-        nodes[tn].label = "tail.o" + std::to_string(tail_start) + "-" + std::to_string(pl.nO - 1);
-        nodes[tn].octave = tail_start;
-        uint64_t tail_bytes = 0;
-        for (int o = tail_start; o < pl.nO; ++o)
-            tail_bytes += (uint64_t)((4.0 * pl.L - 2.875) * (double)pl.oct[o].voxels() * (double)pl.elem);
-        nodes[tn].algo_bytes = tail_bytes;
-        for (int o = tail_start; o < pl.nO; ++o) {
-            const OctaveGeom& g = pl.oct[o];
-            if (g.nx - 2 * pl.p.border < 1 || g.ny - 2 * pl.p.border < 1 || g.nz - 2 * pl.p.border < 1) continue;
-            PeakTmaArgs pa;
-            LaunchSpec ps;
-            if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
-            else ps.name = "peak (DoG tensor map)";
-            peak_nodes.push_back(add(ps, pa, {tn}));
-            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * e * (uint64_t)g.voxels());
-        }
-    }
     SortArgs sa{};
     sa.staging = ws.staging;
-    sa.tail_err = ws.count + 3;
+    sa.err = ws.count + 3;
     sa.out = c.out;
     sa.count = ws.count;
     sa.count_out = ws.count_out;
@@ -830,25 +737,9 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
         cudaError_t e = cudaGraphCreate(&ex.graph, 0);
         if (e != cudaSuccess) return cuda_fail(err, "cudaGraphCreate", e);
         ex.gnodes.resize(ex.nodes.size());
-        // Programmatic (PDL) edges: use_pdl 1 = every kernel-to-kernel edge;
-        // 2 = only edges between kernels of octaves >= 1, whose small grids
-        // are latency bound and leave the SMs mostly free while they wait.
-        const int pdl_mode = ex.profile ? 0 : ws.plan.p.use_pdl;
-
-        auto programmatic = [&](int from, int to) {
-            const Node& a = ex.nodes[from];
-            const Node& b = ex.nodes[to];
-            if (pdl_mode == 0) return false;
-            if (pdl_mode == 1) return true;
-            return a.octave >= 1 && b.octave >= 1;
-        };
         for (size_t i = 0; i < ex.nodes.size(); ++i) {
             std::vector<cudaGraphNode_t> deps;
-            std::vector<int> prog_deps;
-            for (int d : ex.nodes[i].deps) {
-                if (programmatic(d, (int)i)) prog_deps.push_back(d);
-                else deps.push_back(ex.gnodes[d]);
-            }
+            for (int d : ex.nodes[i].deps) deps.push_back(ex.gnodes[d]);
             if (ex.profile) {   // begin event -> kernel -> end event
                 cudaGraphNode_t b;
                 e = cudaGraphAddEventRecordNode(&b, ex.graph, deps.data(), deps.size(), ex.ev_begin[i]);
@@ -856,26 +747,8 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
                 deps.assign(1, b);
             }
             cudaKernelNodeParams kp = node_params(ex.nodes[i]);
-            // A programmatic edge lets the dependent launch while its
-            // predecessor drains; it waits in griddepcontrol.wait.
             e = cudaGraphAddKernelNode(&ex.gnodes[i], ex.graph, deps.data(), deps.size(), &kp);
             if (e != cudaSuccess) return cuda_fail(err, "cudaGraphAddKernelNode", e);
-
-            for (int d : prog_deps) {
-                cudaGraphEdgeData ed{};
-                ed.from_port = cudaGraphKernelNodePortProgrammatic;
-                ed.type = cudaGraphDependencyTypeProgrammatic;
-                e = cudaGraphAddDependencies(ex.graph, &ex.gnodes[d], &ex.gnodes[i], &ed, 1);
-                if (e != cudaSuccess) return cuda_fail(err, "programmatic dependency", e);
-            }
-            if (ex.nodes[i].spec.cluster > 0) {
-                cudaLaunchAttributeValue v{};
-                v.clusterDim.x = (unsigned)ex.nodes[i].spec.cluster;
-                v.clusterDim.y = 1;
-                v.clusterDim.z = 1;
-                e = cudaGraphKernelNodeSetAttribute(ex.gnodes[i], cudaLaunchAttributeClusterDimension, &v);
-                if (e != cudaSuccess) return cuda_fail(err, "cluster kernel node", e);
-            }
             if (ex.profile) {
                 cudaGraphNode_t en;
                 e = cudaGraphAddEventRecordNode(&en, ex.graph, &ex.gnodes[i], 1, ex.ev_end[i]);

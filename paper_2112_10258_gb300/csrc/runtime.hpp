@@ -37,16 +37,7 @@ struct Plan {
     size_t off_TB[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
     size_t bytes = 0;
     uint64_t algo_bytes = 0;
-    int tail_start = 0;              // first octave run by the small-octave kernel (nO: none)
 };
-
-// Largest dynamic shared memory the small-octave kernel may request per CTA.
-constexpr size_t kTailMaxSmem = 200 * 1024;
-// Octaves up to this many voxels go to the small-octave kernel: their passes
-// are launch-latency bound as separate launches, while a cluster's 8-16 SMs
-// keep up with their arithmetic (octave 2 of a 145x174x145 volume, 56K voxels,
-// measured slower in the cluster than as separate launches on all SMs).
-constexpr int64_t kTailMaxVoxels = 32768;
 
 // Validate params (without dims when nx <= 0) and build the plan.
 int validate_params(const sift3d_params& p, std::string* err);
@@ -64,6 +55,7 @@ struct Workspace {
     int* count = nullptr;                 // kDetectCounters ints (see common.cuh)
     int* count_out = nullptr;             // total written by the sort
     int capacity = 0;
+    int* test_flag = nullptr;             // device flag of the timeout test (null: off)
     void* G(int o, int s) const { return base + plan.off_G[o][s]; }
     void* D(int o, int s) const { return base + plan.off_D[o][s]; }
     void* B(int o, int s) const {  // s = 1..S
@@ -77,7 +69,6 @@ size_t workspace_bytes(const Plan& plan, int capacity);
 int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, std::string* err);
 int alloc_device_zeroed(size_t bytes, char** out, std::string* err);
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
-TailArgs make_tail_args(const Workspace& ws);
 PeakArgs make_peak_args(const Workspace& ws, int o);
 // Peak kernel arguments with the octave's DoG tensor map; false if it cannot be encoded.
 bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out);

@@ -29,6 +29,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
+// Arrive on the barrier (one of its expected arrivals), release semantics.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One non-blocking test of phase `parity`.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for phase `parity` of the barrier at most `limit` polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
     for (int i = 0; i < limit; ++i)
@@ -54,31 +70,7 @@ __device__ __forceinline__ void load_4d(void* dst, const CUtensorMap* map, int x
         : "memory");
 }
 
-constexpr int kWaitPolls = 1 << 20;
-
-// One elected thread arms the CTA's barrier for `bytes` and issues the copy
-// `issue()`; every thread then waits (bounded).  Returns false for the whole
-// CTA if the copy did not land in time: the caller's error flag is set and the
-// copy gets a second bounded wait, so no write is in flight when the CTA leaves.
-template <class Issue>
-__device__ __forceinline__ bool stage_tile(uint64_t* bar, unsigned bytes, int* err, Issue issue) {
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar, bytes);
-        issue();
-    }
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kWaitPolls));
-    if (!ok && tid == 0) {
-        atomicExch(err, 1);
-        mbar_wait_bounded(bar, 0, kWaitPolls);
-    }
-    return ok;
-}
+constexpr int kWaitPolls = 1 << 20;   // polls of a bounded wait (each may suspend briefly)
 
 }  // namespace tma
 }  // namespace sift3d

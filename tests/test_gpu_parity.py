@@ -234,23 +234,55 @@ def test_gaussian_blur_matches_oracle(S, shape, sigma):
     det.close()
 
 
-@pytest.mark.parametrize("shape", [(145, 174, 145), (64, 64, 64), (100, 90, 80)])
-def test_octave_tail_kernel_equals_separate_launches(S, shape):
-    """With fuse_small_octaves the last small octaves build their pyramids in
-    one thread-block-cluster launch; every level, DoG, pre-blurred level,
-    keypoint and descriptor must be bitwise what separate launches give."""
-    vol = brain_like_volume(seed=6, shape=shape)
-    outs = []
-    for fuse in (0, 1):
-        det, buf, n, kps = _run(S, vol, fuse_small_octaves=fuse)
-        brief, rrief = det.describe(buf, n)
-        lv = []
-        for o, dims in enumerate(S.plan(*shape)["dims"]):
-            lv.append(det.read_level(o, S.LEVEL_DOG, 2, dims).cpu().numpy().tobytes())
-            lv.append(det.read_level(o, S.LEVEL_DESC, 3, dims).cpu().numpy().tobytes())
-        outs.append((kps.tobytes(), brief[:n].cpu().numpy().tobytes(), rrief[: n * 64].cpu().numpy().tobytes(), lv))
+@pytest.mark.parametrize("cut", [76, 78])
+def test_loosened_sign_sum_cut_matches_oracle(S, brain, cut):
+    """Sec. 2.2.2 "4D Peak Detection": the +-80 interval can be loosened.  A cut
+    below 80 admits non-strict extrema through the kernel's sign-count filter
+    (|s8| + 72 >= cut) instead of the strict max/min test; the sets must equal
+    the oracle's at the same cut up to flagged near ties, on the 64^3 blobs and
+    on 145x174x145."""
+    blobs = blob_volume(seed=0)
+    for vol in (blobs, brain[0]):
+        p = _oracle_params(sign_sum_min=cut)
+        ref = O.detect(vol, p)
+        det, buf, n, kps = _run(S, vol, sign_sum_min=cut)
+        exc, rep = compare_keypoints(kps, ref)
+        strict = O.detect(vol, _oracle_params()) if vol is blobs else brain[2]
+        assert rep["oracle"] > strict.keypoints.size, "the loosened cut admits more keypoints"
+        print(f"cut {cut} {vol.shape}: {rep}")
         det.close()
-    assert outs[0] == outs[1]
+
+
+def test_wider_border_matches_oracle(S):
+    """border = 2 moves the first tile's halo origin and the tested z range."""
+    vol = blob_volume(seed=7, shape=(70, 45, 37), n_blobs=20, sigma_range=(1.5, 4.0))
+    det, buf, n, kps = _run(S, vol, border=2)
+    ref = O.detect(vol, _oracle_params(border=2))
+    compare_keypoints(kps, ref)
+    assert n > 0
+    det.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers(S):
+    """Failure detection without a GPU fault: with test_wait_timeout = 1 the
+    first detect of the context makes the first wait of every peak CTA one
+    non-blocking test, which finds its plane copy still in flight; the CTA sets
+    the error flag, waits for its copies to land and leaves, and sift3d_detect
+    returns SIFT3D_ETIMEDOUT.  The next detect on the same context (same cached
+    graph and workspace) runs normally and matches the oracle."""
+    from paper_2112_10258_gb300 import capi
+    vol = blob_volume(seed=0)
+    d = torch.from_numpy(vol).cuda()
+    det = S.Sift3D(test_wait_timeout=1)
+    out = torch.empty(4096 * 48, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc, n = capi.sift3d_detect(det.ctx, d.data_ptr(), 0, 64, 64, 64, stream, out.data_ptr(), 4096)
+    assert rc == capi.ETIMEDOUT, rc
+    assert "wait" in capi.sift3d_last_error(det.ctx)
+    rc, n = capi.sift3d_detect(det.ctx, d.data_ptr(), 0, 64, 64, 64, stream, out.data_ptr(), 4096)
+    assert rc == capi.OK, rc
+    compare_keypoints(S.keypoints_to_numpy(out, n), O.detect(vol, _oracle_params()))
+    det.close()
 
 
 def test_one_context_many_shapes_shares_its_arena(S):
