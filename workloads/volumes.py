@@ -10,7 +10,8 @@ these generators stand in for it:
 
 * ``blob_volume``   - isotropic Gaussian blobs plus white noise (64^3 detect case).
 * ``brain_like_volume`` - nested ellipsoid shells (0.2/0.5/0.8) warped by a smooth
-  random displacement field, 2000 small blobs, and Rician-like magnitude noise.
+  random displacement field, small blobs at a minimum spacing (6500 on
+  145x174x145), and Rician-like magnitude noise.
 * ``batch_shapes`` / ``poisson_arrivals`` - uneven batch sizes and a request stream.
 
 The smoothing of the displacement field uses an FFT-domain Gaussian transfer
@@ -68,21 +69,70 @@ def _smooth_noise_fft(rng, shape_zyx, sigma: float) -> np.ndarray:
     return np.fft.irfftn(f, s=shape_zyx, axes=(0, 1, 2))
 
 
+BLOB_DENSITY = 6500 / (145 * 174 * 145)   # blobs per voxel of the brain-like family
+
+
+def _spaced_centres(rng, n: int, shape_xyz, min_dist: float) -> np.ndarray:
+    """Up to ``n`` centres uniform in the box, each at least ``min_dist`` from
+    every earlier one (dart throwing over a grid of cells of side min_dist/sqrt(3),
+    which holds at most one centre each)."""
+    nx, ny, nz = shape_xyz
+    if n <= 0:
+        return np.zeros((0, 3))
+    if min_dist <= 0:
+        return rng.uniform([0, 0, 0], [nx - 1, ny - 1, nz - 1], size=(n, 3))
+    cell = min_dist / np.sqrt(3.0)
+    grid = {}
+    out = []
+    reach = int(np.ceil(min_dist / cell))
+    d2 = min_dist * min_dist
+    tries = 0
+    while len(out) < n and tries < 20 * n:
+        batch = rng.uniform([0, 0, 0], [nx - 1, ny - 1, nz - 1], size=(1024, 3))
+        for c in batch:
+            tries += 1
+            key = (int(c[0] // cell), int(c[1] // cell), int(c[2] // cell))
+            ok = True
+            for dx in range(-reach, reach + 1):
+                for dy in range(-reach, reach + 1):
+                    for dz in range(-reach, reach + 1):
+                        q = grid.get((key[0] + dx, key[1] + dy, key[2] + dz))
+                        if q is not None and (q[0] - c[0]) ** 2 + (q[1] - c[1]) ** 2 + (q[2] - c[2]) ** 2 < d2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                grid[key] = c
+                out.append(c)
+                if len(out) == n:
+                    break
+    return np.array(out).reshape(-1, 3)
+
+
 def brain_like_volume(seed: int = 0, shape=BRAIN_SHAPE, warp_sigma: float = 8.0,
                       warp_rms: float = 3.0, semi_axes=(0.45, 0.35, 0.22),
-                      intensities=(0.2, 0.5, 0.8), n_blobs: int = 2000,
-                      blob_sigma=(1.5, 5.0), blob_amp=(0.1, 0.4),
+                      intensities=(0.2, 0.5, 0.8), n_blobs: int | None = None,
+                      blob_sigma=(2.2, 3.5), blob_amp=(0.2, 0.6), blob_min_dist: float = 6.8,
                       noise_std: float = 0.02, dtype=np.float32) -> np.ndarray:
     """Brain-MRI-shaped stand-in for an OASIS-1 T1 volume.
 
     Nested ellipsoids with semi-axes ``semi_axes`` x dims (outer to inner) hold
     intensities 0.2/0.5/0.8; the sampling coordinates are displaced by a smooth
     random field (white noise smoothed at ``warp_sigma`` voxels, scaled so the
-    vector field has ``warp_rms`` voxels RMS); ``n_blobs`` Gaussian blobs with
-    sigma ~ U[blob_sigma] and amplitude +-U[blob_amp] are added; finally
-    Rician-like magnitude noise |I + n1 + i n2|, n ~ N(0, noise_std^2).
+    vector field has ``warp_rms`` voxels RMS); ``n_blobs`` Gaussian blobs (by
+    default 6500 per 145x174x145 voxels, the same density for other shapes)
+    with sigma ~ U[blob_sigma], amplitude +-U[blob_amp] and centres uniform but
+    at least ``blob_min_dist`` voxels apart are added; finally Rician-like
+    magnitude noise |I + n1 + i n2|, n ~ N(0, noise_std^2).  The defaults give
+    about 2900 keypoints on 145x174x145 under the default detector parameters,
+    the paper's per-volume average.
     """
     nx, ny, nz = shape
+    if n_blobs is None:
+        n_blobs = int(round(BLOB_DENSITY * nx * ny * nz))
     rng = np.random.default_rng(seed)
     zyx = (nz, ny, nx)
     d = np.stack([_smooth_noise_fft(rng, zyx, warp_sigma) for _ in range(3)])
@@ -99,10 +149,11 @@ def brain_like_volume(seed: int = 0, shape=BRAIN_SHAPE, warp_sigma: float = 8.0,
         inside = (px / ax) ** 2 + (py / ay) ** 2 + (pz / az) ** 2 <= 1.0
         vol[inside] = inten
     del px, py, pz
-    centres = rng.uniform([0, 0, 0], [nx - 1, ny - 1, nz - 1], size=(n_blobs, 3))
-    sigmas = rng.uniform(blob_sigma[0], blob_sigma[1], size=n_blobs)
-    amps = rng.uniform(blob_amp[0], blob_amp[1], size=n_blobs)
-    amps *= np.where(rng.random(n_blobs) < 0.5, -1.0, 1.0)
+    centres = _spaced_centres(rng, n_blobs, (nx, ny, nz), blob_min_dist)
+    m = len(centres)
+    sigmas = rng.uniform(blob_sigma[0], blob_sigma[1], size=m)
+    amps = rng.uniform(blob_amp[0], blob_amp[1], size=m)
+    amps *= np.where(rng.random(m) < 0.5, -1.0, 1.0)
     _splat_blobs(vol, centres, sigmas, amps)
     n1 = rng.normal(0.0, noise_std, size=zyx)
     n2 = rng.normal(0.0, noise_std, size=zyx)
