@@ -57,9 +57,17 @@ extern "C" {
 #define SIFT3D_DTYPE_F32   0   /* input voxels: float32, used as they are        */
 #define SIFT3D_DTYPE_U8    1   /* input voxels: uint8 codes, converted to c/255  */
 
-#define SIFT3D_STORAGE_F32  0  /* pyramid levels stored in float32               */
-#define SIFT3D_STORAGE_F16  1  /* stored in IEEE half, arithmetic in float32     */
-#define SIFT3D_STORAGE_BF16 2  /* stored in bfloat16, arithmetic in float32      */
+/* Storage of the pyramid.  Arithmetic is float32 in every mode, and the DoG
+ * levels are always stored in float32: with the Gaussian levels in 16 bits,
+ * each DoG D_{s-1} = G_{s-1} - G_s is formed from G_{s-1} as computed (the
+ * stored 16-bit value plus its rounding residual, kept in a 16-bit side
+ * buffer) and G_s before its rounding, so no storage rounding enters the
+ * DoG; rounding the DoG itself to 16 bits would break near ties among the 80
+ * neighbours.  The Gaussian and descriptor levels, the convolution sources
+ * and the octave sub-sampling use the stored 16-bit values. */
+#define SIFT3D_STORAGE_F32  0  /* Gaussian levels stored in float32              */
+#define SIFT3D_STORAGE_F16  1  /* Gaussian levels stored in IEEE half            */
+#define SIFT3D_STORAGE_BF16 2  /* Gaussian levels stored in bfloat16             */
 
 #define SIFT3D_DESC_BRIEF  1
 #define SIFT3D_DESC_RRIEF  2

@@ -31,6 +31,10 @@ blocking or fusion:
   bins, rank normalisation); the details are this implementation's reading.
 * Sub-voxel refinement (one Newton step on the 4D DoG quadratic): not in the
   paper.
+* Reduced-precision storage (not in the paper): ``build_pyramid_stored`` follows
+  the same steps with the Gaussian levels rounded to 16 bits when stored and the
+  DoG formed from each level's value before rounding; it predicts the recall of
+  16-bit storage from the arithmetic alone.
 
 Readings where the paper is silent:
 
@@ -205,6 +209,62 @@ def build_pyramid(vol: np.ndarray, p: Params) -> Pyramid:
 
 
 # ----------------------------------------------------------------------------------
+# Reduced-precision storage (not in the paper): an FP64 emulation of the 16-bit
+# storage scheme, from which the expected recall of FP16 / BF16 storage follows
+# without the GPU.
+# ----------------------------------------------------------------------------------
+
+def round_to_storage(x: np.ndarray, kind: str) -> np.ndarray:
+    """Round to the storage type and return float64: "f64" (unchanged), "f32",
+    "f16" (IEEE half, round to nearest even), "bf16" (the upper 16 bits of the
+    float32 value, round to nearest even)."""
+    x = np.asarray(x, np.float64)
+    if kind == "f64":
+        return x
+    if kind == "f32":
+        return x.astype(np.float32).astype(np.float64)
+    if kind == "f16":
+        return x.astype(np.float16).astype(np.float64)
+    if kind == "bf16":
+        u = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+        u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(kind)
+
+
+def build_pyramid_stored(vol: np.ndarray, p: Params, kind: str) -> Pyramid:
+    """The pyramid of build_pyramid with the Gaussian levels stored as ``kind``:
+    every level is rounded when stored, the next level and the next octave's
+    sub-sample are computed from the stored values, each level's rounding
+    residual (value - stored value) is kept in IEEE half, and each DoG is
+    D_{s-1} = (stored G_{s-1} + its residual) - G_s (G_s before rounding),
+    stored in float32.  With kind "f64" this is build_pyramid exactly."""
+    shapes = octave_shapes(p, vol.shape)
+    incs = increment_sigmas(p)
+    S = p.scales_per_octave
+    exact = kind == "f64"
+    pyr = Pyramid()
+    for o in range(len(shapes)):
+        if o == 0:
+            g = blur3d(input_to_float(vol), initial_sigma(p), p.trunc)
+        else:
+            g = subsample2(pyr.G[o - 1][S])
+        stored = round_to_storage(g, kind)
+        res = g - stored if exact else round_to_storage(g - stored, "f16")
+        levels, dogs = [stored], []
+        for s in range(1, S + 3):
+            gs = blur3d(levels[-1], incs[s - 1], p.trunc)
+            d = (levels[-1] + res) - gs
+            dogs.append(d if exact else round_to_storage(d, "f32"))
+            stored = round_to_storage(gs, kind)
+            res = gs - stored if exact else round_to_storage(gs - stored, "f16")
+            levels.append(stored)
+        pyr.G.append(levels)
+        pyr.D.append(dogs)
+    return pyr
+
+
+# ----------------------------------------------------------------------------------
 # 4D peak detection by sum of signs (Sec. 2.2.2 "4D Peak Detection"), contrast and
 # curvature tests, and near-tie bookkeeping.
 # ----------------------------------------------------------------------------------
@@ -291,7 +351,12 @@ def curvature_test(h, polarity, r, eta=None):
 
 
 def detect(vol: np.ndarray, p: Params, keep_pyramid: bool = True) -> DetectResult:
-    pyr = build_pyramid(vol, p)
+    return detect_pyramid(build_pyramid(vol, p), p, keep_pyramid)
+
+
+def detect_pyramid(pyr: Pyramid, p: Params, keep_pyramid: bool = True) -> DetectResult:
+    """Extrema of a built pyramid: the 80-neighbour sum of signs, the contrast
+    and curvature tests, and the near-tie bookkeeping (Sec. 2.2.2)."""
     S = p.scales_per_octave
     sig = level_sigmas(p)
     rows = []

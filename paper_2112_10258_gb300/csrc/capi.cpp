@@ -655,7 +655,8 @@ int sift3d_read_level(sift3d_ctx* ctx, int octave, int kind, int index, float* d
     a.nz = pl.oct[octave].nz;
     a.dst = dev_dst;
     std::string err;
-    rc = launch(read_level_spec(pl.p.storage, a), &a, static_cast<cudaStream_t>(stream), &err);
+    const int level_storage = kind == SIFT3D_LEVEL_DOG ? SIFT3D_STORAGE_F32 : pl.p.storage;   // DoG: float32
+    rc = launch(read_level_spec(level_storage, a), &a, static_cast<cudaStream_t>(stream), &err);
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
 }
 

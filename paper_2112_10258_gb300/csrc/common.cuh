@@ -50,6 +50,7 @@ struct ConvXYArgs {
     int64_t py, pz;           // pitches of dst / base_out
     int nx, ny, nz;           // dims of this octave
     void* base_out;           // sub mode: G_0 of this octave (storage type), else null
+    __half* res_out;          // sub mode, 16-bit storage: G_0's rounding residual (G_0 - stored G_0)
     int* zero_count;          // if set, block (0,0,0) zeroes kDetectCounters ints first
     Taps taps;
     float* dst2;              // if set: the same plane filtered with taps2 too (the
@@ -68,7 +69,9 @@ struct ConvZArgs {
     const float* src;         // intermediate from conv_xy
     void* dst;                // G_s (storage type)
     const void* prev;         // G_{s-1} for the DoG, or null
-    void* dog;                // D_{s-1} = G_{s-1} - G_s, or null
+    float* dog;               // D_{s-1} = G_{s-1} - G_s (float32 for every storage type), or null
+    __half* res;              // 16-bit storage: rounding residuals, in place: read G_{s-1}'s (when
+                              //   prev is set) and write G_s's; null for float32 storage
     int64_t py, pz;           // shared pitches
     int nx, ny, nz;
     Taps taps;

@@ -80,6 +80,7 @@ template <int R, typename S, int RB>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
     using P = Pair<S>;
     using PT = typename P::T;
+    constexpr bool narrow = sizeof(S) == 2;   // 16-bit storage: residuals travel with the levels
     const int64_t pair = (int64_t)blockIdx.x * Z_THREADS + threadIdx.x;
     const int64_t pz2 = a.pz / 2;
     if (pair >= pz2) return;
@@ -88,33 +89,57 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
     const bool with_dog = a.dog != nullptr;
     float2 v[Z_TZ + 2 * R];
     load_z_window<Z_TZ + 2 * R, R>(reinterpret_cast<const float2*>(a.src) + pair, pz2, z0, a.nz, interior, v);
+    // G_{s-1} as computed, before its rounding to storage: the stored value plus
+    // its rounding residual (16-bit storage), so that the DoG carries no
+    // storage rounding of G_{s-1}
     float2 pv[Z_TZ];
     const PT* prev = static_cast<const PT*>(a.prev) + pair;
+    __half2* res = reinterpret_cast<__half2*>(a.res) + pair;
     if (with_dog) {
         if (z0 + Z_TZ <= a.nz) {   // walk the planes
             const PT* q = prev + (int64_t)z0 * pz2;
+            const __half2* rq = res + (int64_t)z0 * pz2;
 #pragma unroll
             for (int j = 0; j < Z_TZ; ++j) {
                 pv[j] = P::get(*q);
                 q += pz2;
+                if constexpr (narrow) {
+                    const float2 r = __half22float2(*rq);
+                    pv[j] = make_float2(pv[j].x + r.x, pv[j].y + r.y);
+                    rq += pz2;
+                }
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < Z_TZ; ++j) pv[j] = P::get(prev[(int64_t)min(z0 + j, a.nz - 1) * pz2]);
+            for (int j = 0; j < Z_TZ; ++j) {
+                const int64_t zo = (int64_t)min(z0 + j, a.nz - 1) * pz2;
+                pv[j] = P::get(prev[zo]);
+                if constexpr (narrow) {
+                    const float2 r = __half22float2(res[zo]);
+                    pv[j] = make_float2(pv[j].x + r.x, pv[j].y + r.y);
+                }
+            }
         }
     }
     PT* dst = static_cast<PT*>(a.dst) + pair + (int64_t)z0 * pz2;
-    PT* dog = static_cast<PT*>(a.dog) + pair + (int64_t)z0 * pz2;
+    float2* dog = reinterpret_cast<float2*>(a.dog) + pair + (int64_t)z0 * pz2;
+    __half2* rout = res + (int64_t)z0 * pz2;
 #pragma unroll
     for (int j = 0; j < Z_TZ; ++j) {
         if (z0 + j >= a.nz) break;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(a.taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
-        *dst = P::put(acc);
-        if (with_dog) *dog = P::put(make_float2(pv[j].x - acc.x, pv[j].y - acc.y));
+        const PT g = P::put(acc);
+        *dst = g;
+        if constexpr (narrow) {   // acc - stored value, exact in float32
+            const float2 gs = P::get(g);
+            *rout = __floats2half2_rn(acc.x - gs.x, acc.y - gs.y);
+        }
+        if (with_dog) *dog = make_float2(pv[j].x - acc.x, pv[j].y - acc.y);
         dst += pz2;
         dog += pz2;
+        rout += pz2;
     }
     if constexpr (RB > 0) {   // the fused descriptor pre-blur, after the level so registers are reused
         float2 u[Z_TZ + 2 * RB];
@@ -300,9 +325,16 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
             using PB = Pair<Tbase>;
 #pragma unroll
             for (int j = 0; j < RY; ++j)
-                if (y0 + r0 + j < a.ny)
-                    reinterpret_cast<typename PB::T*>(static_cast<Tbase*>(a.base_out) + (int64_t)z * a.pz +
-                                                      (int64_t)(y0 + r0 + j) * a.py + c)[0] = PB::put(v[R + j]);
+                if (y0 + r0 + j < a.ny) {
+                    const int64_t o = (int64_t)z * a.pz + (int64_t)(y0 + r0 + j) * a.py + c;
+                    const typename PB::T g = PB::put(v[R + j]);
+                    reinterpret_cast<typename PB::T*>(static_cast<Tbase*>(a.base_out) + o)[0] = g;
+                    if constexpr (sizeof(Tbase) == 2) {   // rounding residual of the stored G_0
+                        const float2 gs = PB::get(g);
+                        reinterpret_cast<__half2*>(a.res_out + o)[0] =
+                            __floats2half2_rn(v[R + j].x - gs.x, v[R + j].y - gs.y);
+                    }
+                }
         }
 #pragma unroll
         for (int j = 0; j < RY; j += 2) {

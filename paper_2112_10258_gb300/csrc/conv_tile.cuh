@@ -79,9 +79,13 @@ __device__ __forceinline__ void conv_xy_tile(const ConvXYArgs& a, int bx, int by
                 in[r * G::WP + c] = vv[k];
                 if constexpr (SUB) {
                     const int ty = r - R, tx = c - R;
-                    if (ty >= 0 && ty < XY_TY && tx >= 0 && tx < XY_TX && y0 + ty < a.ny && x0 + tx < a.nx)
-                        static_cast<Tbase*>(a.base_out)[(int64_t)z * a.pz + (int64_t)(y0 + ty) * a.py + x0 + tx] =
-                            from_f32<Tbase>(vv[k]);
+                    if (ty >= 0 && ty < XY_TY && tx >= 0 && tx < XY_TX && y0 + ty < a.ny && x0 + tx < a.nx) {
+                        const int64_t o = (int64_t)z * a.pz + (int64_t)(y0 + ty) * a.py + x0 + tx;
+                        const Tbase g = from_f32<Tbase>(vv[k]);
+                        static_cast<Tbase*>(a.base_out)[o] = g;
+                        if constexpr (sizeof(Tbase) == 2)   // rounding residual of the stored G_0
+                            a.res_out[o] = __float2half_rn(vv[k] - to_f32(g));
+                    }
                 }
             }
         }

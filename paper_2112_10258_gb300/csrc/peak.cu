@@ -447,31 +447,22 @@ void peak_geometry(const PeakArgs& a, int* x_start, int* box_x, int* gx, size_t*
 
 }  // namespace
 
-void peak_layout(int storage, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z, int* box_l) {
+void peak_layout(int /*storage*/, const PeakArgs& a, int* x_start, int* box_x, int* box_y, int* box_z, int* box_l) {
     int gx;
     size_t smem;
-    if (storage == SIFT3D_STORAGE_F32) peak_geometry<float>(a, x_start, box_x, &gx, &smem);
-    else peak_geometry<__half>(a, x_start, box_x, &gx, &smem);
+    peak_geometry<float>(a, x_start, box_x, &gx, &smem);   // DoG levels are float32
     *box_y = SY;
     *box_z = SZ;
     *box_l = a.n_scales + 2;   // every DoG level in one copy
 }
 
-LaunchSpec peak_spec(int storage, const PeakTmaArgs& A) {
+LaunchSpec peak_spec(int /*storage: DoG levels are float32 for every storage type*/, const PeakTmaArgs& A) {
     LaunchSpec s;
     const PeakArgs& a = A.a;
     int x_start = 0, box_x = 0, gx = 1;
     size_t smem = 0;
-    if (storage == SIFT3D_STORAGE_F32) {
-        s.func = peak_func<float>(a.n_scales);
-        peak_geometry<float>(a, &x_start, &box_x, &gx, &smem);
-    } else if (storage == SIFT3D_STORAGE_F16) {
-        s.func = peak_func<__half>(a.n_scales);
-        peak_geometry<__half>(a, &x_start, &box_x, &gx, &smem);
-    } else {
-        s.func = peak_func<__nv_bfloat16>(a.n_scales);
-        peak_geometry<__nv_bfloat16>(a, &x_start, &box_x, &gx, &smem);
-    }
+    s.func = peak_func<float>(a.n_scales);
+    peak_geometry<float>(a, &x_start, &box_x, &gx, &smem);
     if (s.func == nullptr || x_start != A.x_start) {
         s.func = nullptr;
         return s;

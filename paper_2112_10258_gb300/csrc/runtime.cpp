@@ -134,10 +134,13 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
     if ((int64_t)pl.oct[0].pz * nz >= (1ll << 31) && pl.nO > 0) return fail(err, "volume too large");
     size_t off = 0;
     for (int o = 0; o < pl.nO; ++o) {
-        const size_t lvl = round_up((size_t)(pl.oct[o].pz * pl.oct[o].nz) * pl.elem, 256);
-        const size_t tmp = round_up((size_t)(pl.oct[o].pz * pl.oct[o].nz) * 4, 256);
+        const size_t vox = (size_t)(pl.oct[o].pz * pl.oct[o].nz);
+        const size_t lvl = round_up(vox * pl.elem, 256);
+        const size_t lvl_d = round_up(vox * Plan::elem_d, 256);
+        const size_t tmp = round_up(vox * 4, 256);
         for (int s = 0; s < pl.L; ++s) { pl.off_G[o][s] = off; off += lvl; }
-        for (int s = 0; s < pl.nD; ++s) { pl.off_D[o][s] = off; off += lvl; }
+        for (int s = 0; s < pl.nD; ++s) { pl.off_D[o][s] = off; off += lvl_d; }
+        if (pl.elem == 2) { pl.off_R[o] = off; off += round_up(vox * 2, 256); }
         if (pl.r_desc > 0)
             for (int s = 0; s < pl.S; ++s) { pl.off_B[o][s] = off; off += lvl; }
         pl.off_T[o] = off;
@@ -149,11 +152,13 @@ int make_plan(const sift3d_params& p, int nx, int ny, int nz, int in_dtype, Plan
 
     // Byte model of the pyramid + DoG + peak path per volume: per octave
     // 1 read of the base, L-1 writes of G_1.., L-2 re-reads of G_1.. as filter
-    // input, L-1 writes and L-1 reads of D, 1 read of G_S, 1/8 write of the next
-    // base; octave 0 also writes G_0 and reads the input at its own width.
-    const double per_octave = 4.0 * pl.L - 2.875;
+    // input, 1 read of G_S, 1/8 write of the next base (Gaussian levels, elem
+    // bytes each), and L-1 writes and L-1 reads of D (elem_d bytes); octave 0
+    // also writes G_0 and reads the input at its own width.
+    const double per_octave_g = 2.0 * pl.L - 0.875, per_octave_d = 2.0 * (pl.L - 1);
     double model = 0.0;
-    for (int o = 0; o < pl.nO; ++o) model += per_octave * (double)pl.oct[o].voxels() * (double)pl.elem;
+    for (int o = 0; o < pl.nO; ++o)
+        model += (per_octave_g * (double)pl.elem + per_octave_d * (double)Plan::elem_d) * (double)pl.oct[o].voxels();
     if (pl.nO > 0) {
         const double in_elem = in_dtype == SIFT3D_DTYPE_U8 ? 1.0 : 4.0;
         const double n0 = (double)pl.oct[0].voxels();
@@ -371,13 +376,6 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
-namespace {
-CUtensorMapDataType map_type(int storage) {
-    return storage == SIFT3D_STORAGE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-           : storage == SIFT3D_STORAGE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-}
-}  // namespace
 
 bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
     const Plan& pl = ws.plan;
@@ -394,9 +392,10 @@ bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
         if (pl.off_D[o][s + 1] - pl.off_D[o][s] != stride) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc == nullptr) return false;
-    const CUtensorMapDataType dt = map_type(pl.p.storage);
+    const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;   // DoG levels are float32
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)pl.nD};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.py * pl.elem, (cuuint64_t)g.pz * pl.elem, (cuuint64_t)stride};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.py * Plan::elem_d, (cuuint64_t)g.pz * Plan::elem_d,
+                                   (cuuint64_t)stride};
     const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)box_l};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = enc(&A.dogs, dt, 4, ws.D(o, 0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -426,6 +425,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         nodes[idx].octave = a;
     };
     const uint64_t e = pl.elem;
+    const uint64_t ed = Plan::elem_d;
     const uint64_t in_e = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 4;
     std::vector<int> peak_nodes;
     int g_node[SIFT3D_MAX_OCTAVES][kMaxLevels];
@@ -462,6 +462,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 xa.src_py = pl.oct[o - 1].py;
                 xa.src_pz = pl.oct[o - 1].pz;
                 xa.base_out = ws.G(o, 0);
+                xa.res_out = ws.Res(o);
                 xa.taps = pl.t_inc[0];
                 radius = pl.r_inc[0];
                 deps.push_back(g_node[o - 1][pl.S]);
@@ -502,8 +503,9 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             za.taps = xa.taps;
             if (s > 0) {
                 za.prev = ws.G(o, s - 1);
-                za.dog = ws.D(o, s - 1);
+                za.dog = static_cast<float*>(ws.D(o, s - 1));
             }
+            za.res = ws.Res(o);
             if (xa.dst2 != nullptr) {
                 za.src2 = ws.TB(o, s - 1);
                 za.dst2 = ws.B(o, s - 1);
@@ -515,7 +517,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 // reads the intermediate, writes G_s; with the DoG also reads
                 // G_{s-1} and writes D_{s-1}; with the fused pre-blur also reads
                 // its intermediate and writes the pre-blurred level
-                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? 2 * e * N : 0) + (za.dst2 ? (4 + e) * N : 0));
+                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? (e + ed) * N : 0) + (za.dst2 ? (4 + e) * N : 0));
             }
             g_node[o][s] = prev;
         }
@@ -528,7 +530,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             else ps.name = "peak (DoG tensor map)";
             peak_nodes.push_back(add(ps, pa, {g_node[o][pl.L - 1]}));
             // the 80-neighbour test reads every DoG level D_0..D_{S+1} in full
-            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * e * (uint64_t)g.voxels());
+            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * ed * (uint64_t)g.voxels());
         }
         // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3), where no level
         // pass fused it

@@ -28,12 +28,14 @@ struct Plan {
     double sig_init = 0, sig_inc[kMaxLevels] = {}, sig_desc = 0;
     int r_init = 0, r_inc[kMaxLevels] = {}, r_desc = 0;
     Taps t_init{}, t_inc[kMaxLevels]{}, t_desc{};
-    size_t elem = 4;                 // bytes per stored pyramid value
+    size_t elem = 4;                 // bytes per stored Gaussian / pre-blurred value
+    static constexpr size_t elem_d = 4;   // bytes per stored DoG value (float32 for every storage type)
     // byte offsets into one workspace allocation
     size_t off_G[SIFT3D_MAX_OCTAVES][kMaxLevels] = {};
     size_t off_D[SIFT3D_MAX_OCTAVES][kMaxDogs] = {};
     size_t off_B[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
     size_t off_T[SIFT3D_MAX_OCTAVES] = {};
+    size_t off_R[SIFT3D_MAX_OCTAVES] = {};   // 16-bit storage: rounding residuals (__half), one level
     size_t off_TB[SIFT3D_MAX_OCTAVES][SIFT3D_MAX_SCALES] = {};
     size_t bytes = 0;
     uint64_t algo_bytes = 0;
@@ -62,6 +64,9 @@ struct Workspace {
         return plan.r_desc > 0 ? (void*)(base + plan.off_B[o][s - 1]) : G(o, s);
     }
     float* T(int o) const { return reinterpret_cast<float*>(base + plan.off_T[o]); }
+    __half* Res(int o) const {   // null for float32 storage
+        return plan.elem == 2 ? reinterpret_cast<__half*>(base + plan.off_R[o]) : nullptr;
+    }
     float* TB(int o, int s) const { return reinterpret_cast<float*>(base + plan.off_TB[o][s - 1]); }
 };
 

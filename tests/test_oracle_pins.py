@@ -658,3 +658,49 @@ def test_siftrank_invariances():
     np.testing.assert_allclose(R3, R0 * np.array([-1.0, -1.0, 1.0]), atol=1e-9)
     perm = np.array([8 * ((k // 8) ^ 3) + ((k % 8) ^ 4) for k in range(64)])
     np.testing.assert_allclose(h3[perm], h0, rtol=1e-9)
+
+
+# ---- reduced-precision storage emulation (not in the paper) -------------------
+
+def test_round_to_storage_matches_the_formats():
+    """bf16 keeps the upper 16 bits of the float32 value with round to nearest,
+    ties to even (8 significant bits: relative error at most 2^-8); f16 is IEEE
+    half (2^-11); f32 is float32 (2^-24)."""
+    one = 1.0
+    cases = [(one + 2 ** -8, one),                    # halfway, even neighbour below
+             (one + 3 * 2 ** -8, one + 2 ** -6),      # halfway, even neighbour above
+             (one + 2 ** -8 + 2 ** -20, one + 2 ** -7),   # just above halfway
+             (-(one + 3 * 2 ** -8), -(one + 2 ** -6)), (0.0, 0.0), (3.0, 3.0)]
+    for x, want in cases:
+        assert O.round_to_storage(np.array([x]), "bf16")[0] == want, x
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-2.0, 2.0, 10000)
+    for kind, eps in (("bf16", 2.0 ** -8), ("f16", 2.0 ** -11), ("f32", 2.0 ** -24)):
+        r = O.round_to_storage(x, kind)
+        assert np.all(np.abs(r - x) <= eps * np.abs(x) * (1 + 1e-12) + (2.0 ** -25 if kind == "f16" else 0.0))
+    assert np.array_equal(O.round_to_storage(x, "f16"), x.astype(np.float16).astype(np.float64))
+    assert np.array_equal(O.round_to_storage(x, "f64"), x)
+
+
+def test_stored_pyramid_emulation():
+    """Without rounding the emulation is build_pyramid exactly; with 16-bit
+    storage the Gaussian levels are representable in the format, and the DoG,
+    formed from the levels before rounding, is far closer to the FP64 DoG than
+    the stored levels are to the FP64 levels."""
+    vol = blob_volume(seed=2, shape=(36, 34, 32), n_blobs=10)
+    p = O.Params(min_octave_dim=16)
+    ref = O.build_pyramid(vol, p)
+    same = O.build_pyramid_stored(vol, p, "f64")
+    for a, b in zip(ref.G + ref.D, same.G + same.D):
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    for kind in ("f16", "bf16"):
+        st = O.build_pyramid_stored(vol, p, kind)
+        for o in range(len(ref.G)):
+            gmax = max(float(np.max(np.abs(g))) for g in ref.G[o])
+            for g in st.G[o]:
+                assert np.array_equal(O.round_to_storage(g, kind), g)
+            g_err = max(float(np.max(np.abs(a - b))) for a, b in zip(st.G[o], ref.G[o]))
+            d_err = max(float(np.max(np.abs(a - b))) for a, b in zip(st.D[o], ref.D[o]))
+            unit = 2.0 ** (-8 if kind == "bf16" else -11)
+            assert g_err <= 4 * unit * gmax
+            assert d_err < 0.5 * g_err, (kind, o, d_err, g_err)
