@@ -81,6 +81,12 @@ extern "C" {
                                   unchanged until the request finishes; the
                                   library copies from it asynchronously (pinned
                                   host memory is read by DMA, no staging copy)  */
+#define SIFT3D_SUBMIT_DEVICE 2 /* submit flag: the volume is device memory of the
+                                  context's GPU, complete when sift3d_submit is
+                                  called (its producer stream synchronised); the
+                                  detect reads it in place, so the caller keeps
+                                  it valid and unchanged until the request
+                                  finishes.  No host-to-device copy.             */
 
 #define SIFT3D_MAX_OCTAVES 16
 #define SIFT3D_MAX_SCALES   5  /* scales_per_octave <= 5                         */
@@ -382,17 +388,24 @@ int sift3d_stage_times(sift3d_ctx* ctx, int max, float* ms_out, const char** nam
  * Errors: SIFT3D_EINVAL (no prior detect or profiling off), SIFT3D_ECUDA. */
 int sift3d_stage_timeline(sift3d_ctx* ctx, int max, float* begin_ms_out, float* end_ms_out, int* n_out);
 
-/* Serving (no counterpart in the paper).  sift3d_submit copies a HOST volume
- * (the library reads it before returning, unless flags has
- * SIFT3D_SUBMIT_NOCOPY) into a request and queues it; the
+/* Serving (no counterpart in the paper).  sift3d_submit queues a volume: by
+ * default a HOST volume, which the library copies before returning (with
+ * SIFT3D_SUBMIT_NOCOPY it reads the caller's buffer later, by DMA); with
+ * SIFT3D_SUBMIT_DEVICE a device volume that the detect reads in place.  The
  * library admits requests to the device while their device memory fits in
  * hbm_budget_bytes and fewer than max_inflight are on the device, runs detect
- * then BRIEF+RRIEF describe for each on its own stream, and copies the results
- * back to host memory.  Requests that overlap in time overlap on the device.
+ * then BRIEF+RRIEF describe for each on its own stream, and a device kernel
+ * writes the count and exactly that many keypoint records and descriptors into
+ * mapped pinned host memory (no round trip to size the copy).  Requests that
+ * overlap in time overlap on the device.
+ *   host_or_dev_vol  x-fastest nx*ny*nz volume of dtype (see flags).
  *   ticket  receives an id for sift3d_poll / sift3d_release.
- * Errors: SIFT3D_EINVAL, SIFT3D_EBUDGET (the volume alone exceeds the budget),
- * SIFT3D_ENOMEM. */
-int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype,
+ * Errors: SIFT3D_EINVAL (also: SIFT3D_SUBMIT_DEVICE with a pointer that is not
+ * device memory of the context's GPU), SIFT3D_EBUDGET (the volume alone exceeds
+ * the budget), SIFT3D_ENOMEM.  Failures while a request runs (allocation,
+ * CUDA) are reported by sift3d_poll for that ticket; later requests are
+ * served normally. */
+int sift3d_submit(sift3d_ctx* ctx, const void* host_or_dev_vol, int dtype,
                   int nx, int ny, int nz, int flags, uint64_t* ticket);
 
 /* Wait up to timeout_us microseconds (0 = do not wait) for a request.  Returns
@@ -404,6 +417,15 @@ int sift3d_poll(sift3d_ctx* ctx, uint64_t ticket, int timeout_us, sift3d_result*
 /* Free the host result of a finished request.  SIFT3D_ENOTFOUND if unknown,
  * SIFT3D_PENDING if it has not finished (nothing is freed). */
 int sift3d_release(sift3d_ctx* ctx, uint64_t ticket);
+
+/* Testing the allocation-failure paths without exhausting memory (no
+ * counterpart in the paper): after this call, the n-th device or pinned host
+ * allocation the library makes (counted from 1, process wide) fails as if out
+ * of memory, once; n = 0 cancels a pending failure.  The call that needed the
+ * allocation returns SIFT3D_ENOMEM (a served request reports it through
+ * sift3d_poll) and releases whatever it had allocated; the context stays
+ * usable.  Returns SIFT3D_OK, or SIFT3D_EINVAL for n < 0. */
+int sift3d_test_fail_allocation(int n);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,8 @@ import numpy as np
 
 from . import capi
 from .capi import (DESC_BOTH, DESC_BRIEF, DESC_RRIEF, DTYPE_F32, DTYPE_U8, KEYPOINT_DTYPE, LEVEL_DESC,
-                   LEVEL_DOG, LEVEL_GAUSS, STORAGE_BF16, STORAGE_F16, STORAGE_F32, SUBMIT_NOCOPY, Sift3DError)
+                   LEVEL_DOG, LEVEL_GAUSS, STORAGE_BF16, STORAGE_F16, STORAGE_F32, SUBMIT_DEVICE, SUBMIT_NOCOPY,
+                   Sift3DError)
 
 __all__ = ["Sift3D", "make_params", "plan", "pattern", "KEYPOINT_DTYPE", "Sift3DError"]
 
@@ -155,6 +156,19 @@ class Sift3D:
         rc, t = capi.sift3d_submit(self.ctx, arr.ctypes.data, dtype, nx, ny, nz, flags)
         self._check(rc, "sift3d_submit")
         return t
+
+    def submit_device(self, vol) -> int:
+        """Queue a CUDA tensor volume (float32 or uint8, shape (nz, ny, nx)); the
+        detect reads it in place, so keep it unchanged until the request ends."""
+        import torch
+        if not vol.is_cuda or not vol.is_contiguous():
+            raise TypeError("vol must be a contiguous CUDA tensor")
+        dtype = DTYPE_U8 if vol.dtype == torch.uint8 else DTYPE_F32
+        if dtype == DTYPE_F32 and vol.dtype != torch.float32:
+            raise TypeError("vol must be float32 or uint8")
+        torch.cuda.current_stream().synchronize()   # the volume is complete before submit
+        nz, ny, nx = vol.shape
+        return self.submit_ptr(vol.data_ptr(), dtype, (nx, ny, nz), flags=SUBMIT_DEVICE)
 
     def submit_ptr(self, ptr: int, dtype: int, dims, flags: int = 0) -> int:
         nx, ny, nz = dims

@@ -21,7 +21,7 @@ DTYPE_F32, DTYPE_U8 = 0, 1
 STORAGE_F32, STORAGE_F16, STORAGE_BF16 = 0, 1, 2
 DESC_BRIEF, DESC_RRIEF, DESC_BOTH = 1, 2, 3
 LEVEL_GAUSS, LEVEL_DOG, LEVEL_DESC = 0, 1, 2
-SUBMIT_NOCOPY = 1
+SUBMIT_NOCOPY, SUBMIT_DEVICE = 1, 2
 MAX_OCTAVES, MAX_SCALES, N_PAIRS = 16, 5, 64
 
 STATUS_NAMES = {OK: "OK", PENDING: "PENDING", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECAPACITY: "ECAPACITY",
@@ -107,6 +107,7 @@ SIGNATURES = {
     "sift3d_match": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
     "sift3d_describe_siftrank": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sift3d_test_fail_allocation": (C.c_int, [C.c_int]),
 }
 
 
@@ -195,6 +196,10 @@ def sift3d_gaussian_blur_noalloc(dev_in, nx, ny, nz, sigma, trunc, dev_out, stre
 
 def sift3d_read_level(ctx, octave, kind, index, dev_dst, stream) -> int:
     return _lib.sift3d_read_level(C.c_void_p(ctx), octave, kind, index, C.c_void_p(dev_dst), C.c_void_p(stream))
+
+
+def sift3d_test_fail_allocation(n: int) -> int:
+    return _lib.sift3d_test_fail_allocation(n)
 
 
 def sift3d_submit(ctx, host_vol_ptr, dtype, nx, ny, nz, flags=0) -> tuple[int, int]:

@@ -168,10 +168,13 @@ struct ServeBuffers {            // device + pinned buffers for one (shape, dtyp
     uint64_t* d_brief = nullptr;
     uint8_t* d_rrief = nullptr;
     void* h_in = nullptr;        // pinned staging of the input
+    // results: mapped pinned host memory, written by the pack kernel through
+    // their device addresses (d_out_*)
     sift3d_keypoint* h_kps = nullptr;
     uint64_t* h_brief = nullptr;
     uint8_t* h_rrief = nullptr;
     int* h_count = nullptr;
+    PackArgs pack{};
     size_t bytes = 0;            // device bytes held
     ~ServeBuffers() {
         cudaFree(d_in);
@@ -265,15 +268,26 @@ struct Server {
         if (*rc != SIFT3D_OK) return nullptr;
         b->ent->ex[r.dtype] = std::make_unique<DetectExec>();
         b->in_bytes = (size_t)r.nx * r.ny * r.nz * (r.dtype == SIFT3D_DTYPE_U8 ? 1 : 4);
-        cudaError_t e = cudaMalloc(&b->d_in, b->in_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_kps, (size_t)cap * sizeof(sift3d_keypoint));
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_brief, (size_t)cap * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_rrief, (size_t)cap * 64);
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_in, b->in_bytes);
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_kps, (size_t)cap * sizeof(sift3d_keypoint));
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_brief, (size_t)cap * 8);
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_rrief, (size_t)cap * 64);
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_count, 2 * sizeof(int));
+        const unsigned mapped = cudaHostAllocMapped;
+        cudaError_t e = dev_alloc(&b->d_in, b->in_bytes);
+        if (e == cudaSuccess) e = dev_alloc((void**)&b->d_kps, (size_t)cap * sizeof(sift3d_keypoint));
+        if (e == cudaSuccess) e = dev_alloc((void**)&b->d_brief, (size_t)cap * 8);
+        if (e == cudaSuccess) e = dev_alloc((void**)&b->d_rrief, (size_t)cap * 64);
+        if (e == cudaSuccess) e = pinned_alloc(&b->h_in, b->in_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = pinned_alloc((void**)&b->h_kps, (size_t)cap * sizeof(sift3d_keypoint), mapped);
+        if (e == cudaSuccess) e = pinned_alloc((void**)&b->h_brief, (size_t)cap * 8, mapped);
+        if (e == cudaSuccess) e = pinned_alloc((void**)&b->h_rrief, (size_t)cap * 64, mapped);
+        if (e == cudaSuccess) e = pinned_alloc((void**)&b->h_count, 2 * sizeof(int), mapped);
+        PackArgs& pk = b->pack;
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&pk.out_kps, b->h_kps, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&pk.out_brief, b->h_brief, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&pk.out_rrief, b->h_rrief, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&pk.out_count, b->h_count, 0);
+        pk.count = b->ent->ws.count_out;
+        pk.capacity = cap;
+        pk.kps = b->d_kps;
+        pk.brief = b->d_brief;
+        pk.rrief = b->d_rrief;
         if (e != cudaSuccess) {
             *err = std::string("serving buffers: ") + cudaGetErrorString(e);
             *rc = e == cudaErrorMemoryAllocation ? SIFT3D_ENOMEM : SIFT3D_ECUDA;
@@ -317,29 +331,29 @@ struct Server {
         cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
         ServeBuffers& b = *r->buf;
         const void* src = r->user_in;
-        if (!(r->flags & SIFT3D_SUBMIT_NOCOPY)) {
-            memcpy(b.h_in, r->host_copy.data(), b.in_bytes);
-            src = b.h_in;
+        const void* vol = b.d_in;
+        cudaError_t e = cudaSuccess;
+        if (r->flags & SIFT3D_SUBMIT_DEVICE) {   // read in place on the device
+            vol = r->user_in;
+        } else {
+            if (!(r->flags & SIFT3D_SUBMIT_NOCOPY)) {
+                memcpy(b.h_in, r->host_copy.data(), b.in_bytes);
+                src = b.h_in;
+            }
+            e = cudaMemcpyAsync(b.d_in, src, b.in_bytes, cudaMemcpyHostToDevice, r->stream);
+            if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
         }
-        cudaError_t e = cudaMemcpyAsync(b.d_in, src, b.in_bytes, cudaMemcpyHostToDevice, r->stream);
-        if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
         if (rc == SIFT3D_OK)
-            rc = enqueue_detect(b.ent.get(), b.d_in, r->dtype, b.d_kps, ctx->p.use_graphs != 0, r->stream, &err);
+            rc = enqueue_detect(b.ent.get(), vol, r->dtype, b.d_kps, ctx->p.use_graphs != 0, r->stream, &err);
         if (rc == SIFT3D_OK)
             rc = enqueue_describe(b.ent.get(), ctx->pattern, b.d_kps, -1, SIFT3D_DESC_BOTH, b.d_brief, b.d_rrief,
                                   r->stream, &err);
-        const int cap = b.ent->ws.capacity;
-        if (rc == SIFT3D_OK) {
-            e = cudaMemcpyAsync(b.h_count, b.ent->ws.count_out, sizeof(int), cudaMemcpyDeviceToHost, r->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b.h_kps, b.d_kps, (size_t)cap * sizeof(sift3d_keypoint), cudaMemcpyDeviceToHost,
-                                    r->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b.h_brief, b.d_brief, (size_t)cap * 8, cudaMemcpyDeviceToHost, r->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b.h_rrief, b.d_rrief, (size_t)cap * 64, cudaMemcpyDeviceToHost, r->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(r->done, r->stream);
-            if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
+        if (rc == SIFT3D_OK) {   // exactly the detected records, written to mapped host memory
+            rc = launch(pack_spec(b.pack), &b.pack, r->stream, &err);
+            if (rc == SIFT3D_OK) {
+                e = cudaEventRecord(r->done, r->stream);
+                if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
+            }
         }
         r->t_admit = now_ms();
         if (rc != SIFT3D_OK) {
@@ -354,7 +368,7 @@ struct Server {
     void retire(Request* r) {
         ServeBuffers& b = *r->buf;
         if (r->status == SIFT3D_OK) {
-            const int total = *b.h_count;
+            const int total = *(volatile int*)b.h_count;
             const int cap = b.ent->ws.capacity;
             r->n_needed = total;
             r->n_kps = std::min(total, cap);
@@ -506,7 +520,7 @@ int sift3d_detect(sift3d_ctx* ctx, const void* dev_vol, int dtype, int nx, int n
     int rc = ensure_device(ctx);
     if (rc != SIFT3D_OK) return rc;
     if (ctx->p.test_wait_timeout > 0 && ctx->test_flag == nullptr) {
-        if (cudaMalloc(&ctx->test_flag, sizeof(int)) != cudaSuccess) {
+        if (dev_alloc((void**)&ctx->test_flag, sizeof(int)) != cudaSuccess) {
             (void)cudaGetLastError();
             ctx->test_flag = nullptr;
             return set_err(ctx, SIFT3D_ENOMEM, "test flag allocation");
@@ -597,7 +611,7 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
         if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
         ctx->blur_scratch = nullptr;
         ctx->blur_scratch_elems = 0;
-        cudaError_t e = cudaMalloc(&ctx->blur_scratch, (size_t)need * 2 * sizeof(float));
+        cudaError_t e = dev_alloc((void**)&ctx->blur_scratch, (size_t)need * 2 * sizeof(float));
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             ctx->blur_scratch = nullptr;
@@ -707,13 +721,21 @@ int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype, int nx, int 
     if (!ctx) return SIFT3D_EINVAL;
     if (!host_vol || !ticket) return set_err(ctx, SIFT3D_EINVAL, "host_vol and ticket must be non-NULL");
     if (dtype != SIFT3D_DTYPE_F32 && dtype != SIFT3D_DTYPE_U8) return set_err(ctx, SIFT3D_EINVAL, "bad dtype");
-    if (flags & ~SIFT3D_SUBMIT_NOCOPY) return set_err(ctx, SIFT3D_EINVAL, "unknown flags");
+    if (flags & ~(SIFT3D_SUBMIT_NOCOPY | SIFT3D_SUBMIT_DEVICE)) return set_err(ctx, SIFT3D_EINVAL, "unknown flags");
     Plan pl;
     std::string err;
     int rc = make_plan(ctx->p, nx, ny, nz, dtype, &pl, &err);
     if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
     rc = ensure_device(ctx);
     if (rc != SIFT3D_OK) return rc;
+    if (flags & SIFT3D_SUBMIT_DEVICE) {   // must be device memory of this context's GPU
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, host_vol) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != ctx->device) {
+            (void)cudaGetLastError();
+            return set_err(ctx, SIFT3D_EINVAL, "SIFT3D_SUBMIT_DEVICE: not device memory of the context's GPU");
+        }
+    }
     if (!ctx->server) ctx->server = std::make_unique<Server>(ctx);
     Server& sv = *ctx->server;
     const uint64_t need = sv.request_bytes(nx, ny, nz, dtype, &err, &rc);
@@ -727,7 +749,7 @@ int sift3d_submit(sift3d_ctx* ctx, const void* host_vol, int dtype, int nx, int 
     r->flags = flags;
     r->t_submit = now_ms();
     const size_t bytes = (size_t)nx * ny * nz * (dtype == SIFT3D_DTYPE_U8 ? 1 : 4);
-    if (flags & SIFT3D_SUBMIT_NOCOPY) {
+    if (flags & (SIFT3D_SUBMIT_NOCOPY | SIFT3D_SUBMIT_DEVICE)) {
         r->user_in = host_vol;
     } else {
         try {
@@ -775,6 +797,12 @@ int sift3d_poll(sift3d_ctx* ctx, uint64_t ticket, int timeout_us, sift3d_result*
     out->keypoints = r->kps.data();
     out->brief = r->brief.data();
     out->rrief = r->rrief.data();
+    return SIFT3D_OK;
+}
+
+int sift3d_test_fail_allocation(int n) {
+    if (n < 0) return SIFT3D_EINVAL;
+    set_allocation_failure(n);
     return SIFT3D_OK;
 }
 

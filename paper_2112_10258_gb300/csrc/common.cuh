@@ -150,6 +150,20 @@ struct MatchArgs {
     int32_t* dist2;            //            second-nearest distance (INT_MAX if none), or null
 };
 
+// Results of a served request into mapped pinned host memory: the total
+// count and exactly min(count, capacity) records and descriptors.
+struct PackArgs {
+    const int* count;                  // device: keypoints detected (< 0: the detect failed)
+    int capacity;
+    const sift3d_keypoint* kps;        // device arrays of capacity entries
+    const uint64_t* brief;
+    const uint8_t* rrief;
+    int* out_count;                    // mapped host memory (device addresses)
+    sift3d_keypoint* out_kps;
+    uint64_t* out_brief;
+    uint8_t* out_rrief;
+};
+
 struct ReadLevelArgs {
     const void* src;
     int64_t py, pz;
@@ -177,6 +191,7 @@ LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
+LaunchSpec pack_spec(const PackArgs& a);
 LaunchSpec match_spec(int kind, const MatchArgs& a);
 // SIFT-Rank descriptors of keypoints on the levels of d.lv (G_s, not pre-blurred).
 int enqueue_siftrank(int storage, const DescribeArgs& d, const sift3d_keypoint* kps, int n, const int* n_dev,

@@ -330,7 +330,36 @@ __global__ void read_level_kernel(const ReadLevelArgs a) {
     }
 }
 
+// One CTA of 256 threads per 64 records: 16-byte words of the records (3 per
+// keypoint), the BRIEF words and the RRIEF rows (4 per keypoint), grid-strided.
+__global__ void pack_results_kernel(const PackArgs a) {
+    const int total = *a.count;
+    const int n = total < 0 ? 0 : min(total, a.capacity);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.out_count = total;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4* ks = reinterpret_cast<const uint4*>(a.kps);
+    uint4* kd = reinterpret_cast<uint4*>(a.out_kps);
+    for (int64_t i = t0; i < (int64_t)n * 3; i += stride) kd[i] = ks[i];
+    if (a.out_brief != nullptr)
+        for (int64_t i = t0; i < n; i += stride) a.out_brief[i] = a.brief[i];
+    if (a.out_rrief != nullptr) {
+        const uint4* rs = reinterpret_cast<const uint4*>(a.rrief);
+        uint4* rd = reinterpret_cast<uint4*>(a.out_rrief);
+        for (int64_t i = t0; i < (int64_t)n * 4; i += stride) rd[i] = rs[i];
+    }
+}
+
 }  // namespace
+
+LaunchSpec pack_spec(const PackArgs& a) {
+    LaunchSpec s;
+    s.func = reinterpret_cast<const void*>(&pack_results_kernel);
+    s.grid = dim3((unsigned)std::max(1, std::min(148, (a.capacity + 63) / 64)));
+    s.block = dim3(256);
+    s.name = "pack_results";
+    return s;
+}
 
 LaunchSpec describe_spec(int storage, const DescribeArgs&, int n_max) {
     LaunchSpec s;

@@ -5,6 +5,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -301,9 +302,38 @@ int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, st
     return SIFT3D_OK;
 }
 
+namespace {
+std::atomic<int> g_fail_countdown{0};   // > 0: allocations left until the one that fails
+
+bool injected_failure() {
+    int n = g_fail_countdown.load();
+    while (n > 0)
+        if (g_fail_countdown.compare_exchange_weak(n, n - 1)) return n == 1;
+    return false;
+}
+}  // namespace
+
+void set_allocation_failure(int n) { g_fail_countdown.store(n > 0 ? n : 0); }
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_alloc(void** p, size_t bytes, unsigned flags) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaHostAlloc(p, bytes, flags);
+}
+
 int alloc_device_zeroed(size_t bytes, char** out, std::string* err) {
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_alloc(&p, bytes);
     if (e == cudaSuccess) e = cudaMemset(p, 0, bytes);   // padding columns start finite
     if (e != cudaSuccess) {
         if (p) cudaFree(p);

@@ -70,6 +70,12 @@ struct Workspace {
     float* TB(int o, int s) const { return reinterpret_cast<float*>(base + plan.off_TB[o][s - 1]); }
 };
 
+// Every device and pinned host allocation of the library goes through these,
+// so that a test can make the n-th one fail (sift3d_test_fail_allocation).
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t pinned_alloc(void** p, size_t bytes, unsigned flags);
+void set_allocation_failure(int n);
+
 size_t workspace_bytes(const Plan& plan, int capacity);
 int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, std::string* err);
 int alloc_device_zeroed(size_t bytes, char** out, std::string* err);

@@ -163,3 +163,11 @@ def test_match_rejects_bad_arguments_without_device(lib):
     assert capi.sift3d_match(0, -1, 0, 4, 1, 0, 0, 0, 0) == capi.EINVAL     # negative count
     assert capi.sift3d_match(0, 4, 0, 4, 1, 0, 0, 0, 0) == capi.EINVAL      # NULL pointers
     assert capi.sift3d_match(8, 4, 8, 4, 2, 16, 16, 0, 0) == capi.EINVAL    # RRIEF rows not 16-byte aligned
+
+
+def test_allocation_failure_hook_arguments(lib):
+    """The test hook takes n >= 0 (0 cancels) and needs no device."""
+    from paper_2112_10258_gb300 import capi
+    assert capi.sift3d_test_fail_allocation(-1) == capi.EINVAL
+    assert capi.sift3d_test_fail_allocation(5) == capi.OK
+    assert capi.sift3d_test_fail_allocation(0) == capi.OK

@@ -89,3 +89,21 @@ def test_capacity_reported_in_result(S):
     r = _wait(srv, t)
     assert r["status"] == -3 and r["n_keypoints"] == 3 and r["n_needed"] > 3
     srv.close()
+
+
+def test_device_resident_submit_matches_host_submit(S):
+    """SIFT3D_SUBMIT_DEVICE: the request reads a CUDA volume in place (no
+    host-to-device copy); results equal the host submit's, for float32 and uint8."""
+    srv = S.Sift3D(max_inflight=2)
+    for vol in (brain_like_volume(seed=8, shape=(80, 72, 64)), to_uint8(brain_like_volume(seed=9, shape=(64, 60, 56)))):
+        host = _wait(srv, srv.submit(vol))
+        d = torch.from_numpy(vol).cuda()
+        dev = _wait(srv, srv.submit_device(d))
+        assert host["status"] == dev["status"] == 0
+        assert host["keypoints"].tobytes() == dev["keypoints"].tobytes()
+        assert np.array_equal(host["brief"], dev["brief"]) and np.array_equal(host["rrief"], dev["rrief"])
+    with pytest.raises(S.Sift3DError) as e:   # a host pointer is not device memory
+        srv.submit_ptr(brain_like_volume(seed=8, shape=(16, 16, 16)).ctypes.data, S.DTYPE_F32, (16, 16, 16),
+                       flags=S.SUBMIT_DEVICE)
+    assert e.value.code == -1
+    srv.close()
