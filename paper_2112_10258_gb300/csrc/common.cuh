@@ -85,7 +85,9 @@ struct PeakArgs {
     const void* dog[kMaxDogs];   // D_0..D_{S+1} of the octave (storage type)
     int64_t py, pz;
     int nx, ny, nz;
-    int octave, n_scales, border, sign_sum_min;
+    int octave, n_scales, border, sign_sum_min;   // n_scales: S, the octave's scales
+    int ns, scale_base;                 // this launch tests scales scale_base+1 .. scale_base+ns,
+                                        // staged as DoG levels scale_base .. scale_base+ns+1
     float contrast, curv_k1, curv_k2;   // (2r+1)^3 and r^2
     float sigma_level[kMaxLevels];      // sigma_s in octave voxels
     int refine;                         // report the 4D quadratic's extremum

@@ -229,12 +229,13 @@ __device__ __forceinline__ void write_keypoint(const PeakArgs& a, int slot, int 
     k.x = ((float)x + off[0] + 0.5f) * scale - 0.5f;
     k.y = ((float)y + off[1] + 0.5f) * scale - 0.5f;
     k.z = ((float)z + off[2] + 0.5f) * scale - 0.5f;
-    k.sigma = a.sigma_level[s] * (refined == 1 ? exp2f(off[3] / (float)a.n_scales) : 1.0f) * scale;
+    const int so = s + a.scale_base;   // the octave's scale index
+    k.sigma = a.sigma_level[so] * (refined == 1 ? exp2f(off[3] / (float)a.n_scales) : 1.0f) * scale;
     k.ix = x;
     k.iy = y;
     k.iz = z;
     k.octave = (int16_t)a.octave;
-    k.scale = (int16_t)s;
+    k.scale = (int16_t)so;
     k.polarity = ssum > 0 ? 1 : -1;
     k.refined = (int8_t)refined;
     k.reserved0[0] = k.reserved0[1] = 0;
@@ -385,11 +386,12 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
 // ---- canonical order ------------------------------------------------------
 // Rank sort: the key of record i packs (octave, scale, iz, iy, ix, i), so keys
 // are unique and record i's place is the number of smaller keys.  Each CTA
-// ranks 128 records against all keys, read through shared memory in tiles that
-// all 1024 threads stage at once; the 8 consecutive lanes of a record each count
-// every 8th key and add their counts.
-constexpr int SORT_RECORDS = 128;
-constexpr int SORT_LANES = 8;
+// ranks 32 records against all keys, read through shared memory in tiles that
+// all 512 threads stage at once; the 16 consecutive lanes of a record each
+// count every 16th key and add their counts.  Small CTAs spread a few thousand
+// records over many SMs: the sort closes the detect's critical path.
+constexpr int SORT_RECORDS = 32;
+constexpr int SORT_LANES = 16;
 constexpr int SORT_THREADS = SORT_RECORDS * SORT_LANES;
 constexpr int SORT_TILE = kSortSmemKeys;
 
@@ -442,7 +444,7 @@ void peak_geometry(const PeakArgs& a, int* x_start, int* box_x, int* gx, size_t*
     *box_x = box_w<S>();
     const int covered = a.nx - a.border - (*x_start + 1);    // x = x_start+1 .. nx-border-1
     *gx = std::max(1, (covered + TX - 1) / TX);
-    *smem = peak_smem<S>(a.n_scales + 2);
+    *smem = peak_smem<S>(a.ns + 2);
 }
 
 }  // namespace
@@ -453,7 +455,7 @@ void peak_layout(int /*storage*/, const PeakArgs& a, int* x_start, int* box_x, i
     peak_geometry<float>(a, x_start, box_x, &gx, &smem);   // DoG levels are float32
     *box_y = SY;
     *box_z = SZ;
-    *box_l = a.n_scales + 2;   // every DoG level in one copy
+    *box_l = a.ns + 2;   // the launch's DoG levels in one copy
 }
 
 LaunchSpec peak_spec(int /*storage: DoG levels are float32 for every storage type*/, const PeakTmaArgs& A) {
@@ -461,7 +463,7 @@ LaunchSpec peak_spec(int /*storage: DoG levels are float32 for every storage typ
     const PeakArgs& a = A.a;
     int x_start = 0, box_x = 0, gx = 1;
     size_t smem = 0;
-    s.func = peak_func<float>(a.n_scales);
+    s.func = peak_func<float>(a.ns);
     peak_geometry<float>(a, &x_start, &box_x, &gx, &smem);
     if (s.func == nullptr || x_start != A.x_start) {
         s.func = nullptr;

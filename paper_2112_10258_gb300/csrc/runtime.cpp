@@ -375,6 +375,8 @@ PeakArgs make_peak_args(const Workspace& ws, int o) {
     pa.nz = g.nz;
     pa.octave = o;
     pa.n_scales = pl.S;
+    pa.ns = pl.S;
+    pa.scale_base = 0;
     pa.border = pl.p.border;
     pa.sign_sum_min = pl.p.sign_sum_min;
     pa.contrast = (float)pl.p.contrast_thresh;
@@ -407,28 +409,31 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 
-bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out) {
+bool make_peak_tma_args(const Workspace& ws, int o, int first_scale, int ns, PeakTmaArgs* out) {
     const Plan& pl = ws.plan;
     const OctaveGeom& g = pl.oct[o];
     PeakTmaArgs& A = *out;
     memset(&A, 0, sizeof(A));
     A.a = make_peak_args(ws, o);
+    A.a.ns = ns;
+    A.a.scale_base = first_scale - 1;
     A.err = ws.count + 3;
     int box_x, box_y, box_z, box_l;
     peak_layout(pl.p.storage, A.a, &A.x_start, &box_x, &box_y, &box_z, &box_l);
     A.test_flag = ws.test_flag;
+    const int l0 = first_scale - 1, nl = ns + 2;   // staged DoG levels l0 .. l0+nl-1
     const size_t stride = pl.off_D[o][1] - pl.off_D[o][0];
-    for (int s = 1; s + 1 < pl.nD; ++s)
+    for (int s = l0; s + 1 < l0 + nl; ++s)
         if (pl.off_D[o][s + 1] - pl.off_D[o][s] != stride) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc == nullptr) return false;
     const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;   // DoG levels are float32
-    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)pl.nD};
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nl};
     const cuuint64_t strides[3] = {(cuuint64_t)g.py * Plan::elem_d, (cuuint64_t)g.pz * Plan::elem_d,
                                    (cuuint64_t)stride};
     const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_z, (cuuint32_t)box_l};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = enc(&A.dogs, dt, 4, ws.D(o, 0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUresult r = enc(&A.dogs, dt, 4, ws.D(o, l0), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -552,15 +557,23 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             g_node[o][s] = prev;
         }
         if (o > 0) g_node[o][0] = g_node[o][1];
-        // peak detection on D_1..D_S
+        // peak detection on D_1..D_S.  Octave 0 tests each scale s in its own
+        // launch as soon as D_{s+1} exists (after level s+2), so scales 1..S-1
+        // overlap the remaining level passes; the smaller octaves test all
+        // scales in one launch after their last level.
         if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
-            PeakTmaArgs pa;
-            LaunchSpec ps;
-            if (make_peak_tma_args(ws, o, &pa)) ps = peak_spec(st, pa);
-            else ps.name = "peak (DoG tensor map)";
-            peak_nodes.push_back(add(ps, pa, {g_node[o][pl.L - 1]}));
-            // the 80-neighbour test reads every DoG level D_0..D_{S+1} in full
-            tag(peak_nodes.back(), "o%d.d%d.%s", o, pl.S, (uint64_t)pl.nD * ed * (uint64_t)g.voxels());
+            const bool per_scale = o == 0 && pl.S > 1;
+            for (int s0 = 1; s0 <= pl.S; s0 += per_scale ? 1 : pl.S) {
+                const int ns = per_scale ? 1 : pl.S;
+                PeakTmaArgs pa;
+                LaunchSpec ps;
+                if (make_peak_tma_args(ws, o, s0, ns, &pa)) ps = peak_spec(st, pa);
+                else ps.name = "peak (DoG tensor map)";
+                peak_nodes.push_back(add(ps, pa, {g_node[o][s0 + ns + 1]}));
+                // the 80-neighbour test reads its ns + 2 DoG levels in full
+                tag(peak_nodes.back(), per_scale ? "o%d.d%d.%s" : "o%d.d1-%d.%s", o, per_scale ? s0 : pl.S,
+                    (uint64_t)(ns + 2) * ed * (uint64_t)g.voxels());
+            }
         }
         // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3), where no level
         // pass fused it

@@ -81,8 +81,9 @@ int bind_workspace(const Plan& plan, int capacity, char* base, Workspace* ws, st
 int alloc_device_zeroed(size_t bytes, char** out, std::string* err);
 int alloc_workspace(const Plan& plan, int capacity, Workspace* ws, std::string* err);
 PeakArgs make_peak_args(const Workspace& ws, int o);
-// Peak kernel arguments with the octave's DoG tensor map; false if it cannot be encoded.
-bool make_peak_tma_args(const Workspace& ws, int o, PeakTmaArgs* out);
+// Peak kernel arguments with the DoG tensor map of octave o for a launch that
+// tests scales first_scale .. first_scale+ns-1; false if it cannot be encoded.
+bool make_peak_tma_args(const Workspace& ws, int o, int first_scale, int ns, PeakTmaArgs* out);
 void free_workspace(Workspace* ws);
 
 // One kernel launch of the detect DAG with its argument bytes and dependencies.
