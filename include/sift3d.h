@@ -152,6 +152,15 @@ typedef struct sift3d_params {
                                     and sift3d_detect returns
                                     SIFT3D_ETIMEDOUT.  Later detects on the
                                     same context run normally.  0..1000.     */
+    int32_t  autotune;           /* 1 (default): at the first detect of a
+                                    volume shape (outside stream capture),
+                                    time each full-row y/x pass at tile
+                                    heights of 8, 16 and 32 rows with CUDA
+                                    events and keep the fastest (cached per
+                                    process); results are bitwise the same
+                                    for every height.  0 = 16 rows.          */
+    int32_t  conv_row_tile;      /* 0 (default): as autotune says; 8, 16, 24
+                                    or 32 = rows per CTA of the y/x pass      */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

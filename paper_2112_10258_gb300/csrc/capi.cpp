@@ -459,6 +459,8 @@ int sift3d_default_params(sift3d_params* out) {
     out->max_keypoints = 8192;
     out->max_inflight = 4;
     out->test_wait_timeout = 0;
+    out->autotune = 1;
+    out->conv_row_tile = 0;
     out->refine = 0;
     return SIFT3D_OK;
 }

@@ -55,6 +55,7 @@ struct ConvXYArgs {
     Taps taps;
     float* dst2;              // if set: the same plane filtered with taps2 too (the
     Taps taps2;               //   descriptor pre-blur, radius kFusedBlurRadius)
+    int row_tile;             // rows per CTA of the full-row kernel (multiple of 8; 0: 16)
 };
 
 // Radius of the descriptor pre-blur that the level kernels can fuse (sigma 0.95).
@@ -187,7 +188,7 @@ cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st);
 
 // Launch builders (one per kernel family).  `storage` is SIFT3D_STORAGE_*,
 // `src_kind` for conv_xy is 0 = float32, 1 = uint8, 2 = storage type.
-LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const ConvXYArgs& a);
+LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYArgs& a);   // sets a.row_tile
 LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a);
 LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
 //         (Sec. 2.2.2 "Sub-sampling"), and the CTA's own rows of the means are
 //         written to base_out as the octave's G_0.
 constexpr int RY = 8;                 // rows per y task
-constexpr int ROW_TY = 2 * RY;        // rows per CTA
+constexpr int ROW_TY = 2 * RY;        // default rows per CTA (ConvXYArgs.row_tile: a multiple of RY)
 
 __host__ __device__ constexpr int row_apron(int R) { return R + (R & 1); }
 
@@ -192,14 +192,18 @@ __host__ __device__ constexpr int row_line(int nx, int R) {
     return w + ((2 - (w & 3)) & 3);
 }
 
-__host__ __device__ constexpr int row_smem(int nx, int R, int RB) {
-    return (RB > 0 ? 2 : 1) * (ROW_TY / 2) * row_line(nx, R) * 8;
+__host__ __device__ constexpr int row_smem(int nx, int R, int RB, int ty) {
+    return (RB > 0 ? 2 : 1) * (ty / 2) * row_line(nx, R) * 8;
 }
 
-__host__ __device__ constexpr int row_threads(int nx) {
+// Threads of a row CTA of ty rows: enough for every y task (column pair x
+// RY rows) or every x task (row pair x 8 columns) in one round, at most
+// ROW_MAX_NX; the passes loop over their tasks.
+__host__ __device__ constexpr int row_threads(int nx, int ty) {
     const int pairs = (nx + 1) / 2, groups = (nx + 7) / 8;
-    const int t = 2 * pairs > 8 * groups ? 2 * pairs : 8 * groups;
-    return (t + 31) / 32 * 32;
+    const int ytasks = pairs * (ty / RY), xtasks = (ty / 2) * groups;
+    const int t = ((ytasks > xtasks ? ytasks : xtasks) + 31) / 32 * 32;
+    return t < ROW_MAX_NX ? t : ROW_MAX_NX;
 }
 
 template <typename Tin>
@@ -274,9 +278,11 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
     const int nx = a.nx;
     const int W = row_line(nx, R);
     constexpr int RA = row_apron(R);
-    float2* mid = rows_sm;                              // [ROW_TY/2][W]
-    float2* mid2 = rows_sm + (ROW_TY / 2) * W;          // same, pre-blur (RB > 0)
-    const int y0 = blockIdx.x * ROW_TY;
+    const int ty = a.row_tile;                          // rows of this CTA (multiple of RY)
+    const int nlines = ty / 2;                          // row-pair lines
+    float2* mid = rows_sm;                              // [nlines][W]
+    float2* mid2 = rows_sm + nlines * W;                // same, pre-blur (RB > 0)
+    const int y0 = blockIdx.x * ty;
     const int z = blockIdx.y;
     const int tid = threadIdx.x;
     const Tin* src = static_cast<const Tin*>(a.src);
@@ -284,8 +290,8 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
 
     // y pass
     const int pairs = (nx + 1) / 2;
-    if (tid < 2 * pairs) {
-        const int h = tid >= pairs ? 1 : 0, p = tid - h * pairs;
+    for (int task = tid; task < pairs * (ty / RY); task += blockDim.x) {
+        const int h = task / pairs, p = task - h * pairs;
         const int c = 2 * p, r0 = h * RY;
         const bool full = c + 1 < nx;
         const int gy0 = y0 + r0 - R;   // first source row
@@ -367,8 +373,8 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
         const int per_line = RA + right;
         const int nb = RB > 0 ? 2 : 1;
         const int lane = tid & 31, nwarps = blockDim.x >> 5;   // blockDim.x is a multiple of 32
-        for (int l = tid >> 5; l < nb * (ROW_TY / 2); l += nwarps) {   // a warp per line
-            float2* line = (l < ROW_TY / 2 ? mid : mid2) + (l % (ROW_TY / 2)) * W;
+        for (int l = tid >> 5; l < nb * nlines; l += nwarps) {   // a warp per line
+            float2* line = (l < nlines ? mid : mid2) + (l % nlines) * W;
             for (int e = lane; e < per_line; e += 32) {
                 if (e < RA) line[e] = line[RA];
                 else line[RA + nx + (e - RA)] = line[RA + nx - 1];
@@ -379,9 +385,9 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
 
     // x pass
     const int groups = (nx + ROW_J - 1) / ROW_J;
-    for (int item = tid; item < (ROW_TY / 2) * groups; item += blockDim.x) {
-        const int rp = item % (ROW_TY / 2);
-        const int g = item / (ROW_TY / 2);
+    for (int item = tid; item < nlines * groups; item += blockDim.x) {
+        const int rp = item % nlines;
+        const int g = item / nlines;
         const int x0 = g * ROW_J;
         const int y = y0 + 2 * rp;
         if (y >= a.ny) continue;
@@ -403,19 +409,19 @@ const void* xy_func_table(int r, int* smem, std::integer_sequence<int, Rs...>) {
 }
 
 template <int MODE, typename Tin, typename Tbase, int... Rs>
-const void* row_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
+const void* row_func_table(int r, int nx, int ty, int* smem, std::integer_sequence<int, Rs...>) {
     const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + 1, MODE, Tin, Tbase, 0>)...};
-    *smem = row_smem(nx, r, 0);
+    *smem = row_smem(nx, r, 0, ty);
     return fns[r - 1];
 }
 
 // Fused pre-blur variants exist for radii >= kFusedBlurRadius (index r-RB).
 template <typename Tin, int... Rs>
-const void* row_blur_func_table(int r, int nx, int* smem, std::integer_sequence<int, Rs...>) {
+const void* row_blur_func_table(int r, int nx, int ty, int* smem, std::integer_sequence<int, Rs...>) {
     constexpr int RB = kFusedBlurRadius;
     const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + RB, 0, Tin, float, RB>)...};
     if (r < RB) return nullptr;
-    *smem = row_smem(nx, r, RB);
+    *smem = row_smem(nx, r, RB, ty);
     return fns[r - RB];
 }
 
@@ -443,44 +449,46 @@ const void* xy_func(int r, int* smem) {
 }
 
 template <int MODE, typename Tin, typename Tbase>
-const void* row_func(int r, int nx, int* smem) {
-    return row_func_table<MODE, Tin, Tbase>(r, nx, smem, RadiusSeq{});
+const void* row_func(int r, int nx, int ty, int* smem) {
+    return row_func_table<MODE, Tin, Tbase>(r, nx, ty, smem, RadiusSeq{});
 }
 
 }  // namespace
 
-LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, const ConvXYArgs& a) {
+LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYArgs& a) {
     LaunchSpec s;
     int smem = 0;
     if (radius < 1 || radius > kMaxRadius) return s;
+    if (a.row_tile < RY || a.row_tile % RY != 0 || a.row_tile > 64) a.row_tile = ROW_TY;
+    const int ty = a.row_tile;
     if (a.dst2 != nullptr) {   // level pass with the descriptor pre-blur fused in
         if (sub || src_kind != 2 || a.nx > ROW_MAX_NX) return s;
-        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<float>(radius, a.nx, &smem, BlurRadiusSeq{});
-        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<__half>(radius, a.nx, &smem, BlurRadiusSeq{});
-        else s.func = row_blur_func_table<__nv_bfloat16>(radius, a.nx, &smem, BlurRadiusSeq{});
+        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<float>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
+        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<__half>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
+        else s.func = row_blur_func_table<__nv_bfloat16>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
         if (s.func == nullptr) return s;
         if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
-        s.block = dim3(row_threads(a.nx));
+        s.grid = dim3((a.ny + ty - 1) / ty, a.nz, 1);
+        s.block = dim3(row_threads(a.nx, ty));
         s.smem = smem;
         s.name = "conv_xy_blur";
         return s;
     }
     if (a.nx <= ROW_MAX_NX) {
         if (!sub) {
-            if (src_kind == 0) s.func = row_func<1, float, float>(radius, a.nx, &smem);
-            else if (src_kind == 1) s.func = row_func<1, uint8_t, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F32) s.func = row_func<0, float, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<0, __half, float>(radius, a.nx, &smem);
-            else s.func = row_func<0, __nv_bfloat16, float>(radius, a.nx, &smem);
+            if (src_kind == 0) s.func = row_func<1, float, float>(radius, a.nx, ty, &smem);
+            else if (src_kind == 1) s.func = row_func<1, uint8_t, float>(radius, a.nx, ty, &smem);
+            else if (storage == SIFT3D_STORAGE_F32) s.func = row_func<0, float, float>(radius, a.nx, ty, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<0, __half, float>(radius, a.nx, ty, &smem);
+            else s.func = row_func<0, __nv_bfloat16, float>(radius, a.nx, ty, &smem);
         } else {
-            if (storage == SIFT3D_STORAGE_F32) s.func = row_func<2, float, float>(radius, a.nx, &smem);
-            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<2, __half, __half>(radius, a.nx, &smem);
-            else s.func = row_func<2, __nv_bfloat16, __nv_bfloat16>(radius, a.nx, &smem);
+            if (storage == SIFT3D_STORAGE_F32) s.func = row_func<2, float, float>(radius, a.nx, ty, &smem);
+            else if (storage == SIFT3D_STORAGE_F16) s.func = row_func<2, __half, __half>(radius, a.nx, ty, &smem);
+            else s.func = row_func<2, __nv_bfloat16, __nv_bfloat16>(radius, a.nx, ty, &smem);
         }
         if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        s.grid = dim3((a.ny + ROW_TY - 1) / ROW_TY, a.nz, 1);
-        s.block = dim3(row_threads(a.nx));
+        s.grid = dim3((a.ny + ty - 1) / ty, a.nz, 1);
+        s.block = dim3(row_threads(a.nx, ty));
         s.smem = smem;
         s.name = sub ? "conv_xy_sub" : "conv_xy";
         return s;

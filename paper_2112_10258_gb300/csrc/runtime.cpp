@@ -6,6 +6,9 @@
 #include <cudaTypedefs.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -75,6 +78,10 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.max_inflight < 1 || p.max_inflight > 64) return fail(err, "max_inflight must be in 1..64");
     if (p.refine < 0 || p.refine > 1) return fail(err, "refine must be 0 or 1");
     if (p.test_wait_timeout < 0 || p.test_wait_timeout > 1000) return fail(err, "test_wait_timeout must be in 0..1000");
+    if (p.autotune < 0 || p.autotune > 1) return fail(err, "autotune must be 0 or 1");
+    if (p.conv_row_tile != 0 && p.conv_row_tile != 8 && p.conv_row_tile != 16 && p.conv_row_tile != 24 &&
+        p.conv_row_tile != 32)
+        return fail(err, "conv_row_tile must be 0, 8, 16, 24 or 32");
 
     // filter radii of the schedule
     const int S = p.scales_per_octave;
@@ -518,7 +525,10 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 xa.taps2 = pl.t_desc;
                 fused[o][s - 1] = true;
             }
-            const int nxy = add(conv_xy_spec(radius, src_kind, st, sub, xa), xa, deps);
+            xa.row_tile = pl.p.conv_row_tile;
+            const LaunchSpec xspec = conv_xy_spec(radius, src_kind, st, sub, xa);   // sets xa.row_tile
+            const int nxy = add(xspec, xa, deps);
+            nodes[nxy].xy = {radius, src_kind, sub, true};
             if (*first_node < 0) *first_node = nxy;
             {
                 const uint64_t N = (uint64_t)g.voxels();
@@ -592,7 +602,10 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 xa.ny = g.ny;
                 xa.nz = g.nz;
                 xa.taps = pl.t_desc;
-                const int nxy = add(conv_xy_spec(pl.r_desc, 2, st, false, xa), xa, {g_node[o][s]});
+                xa.row_tile = pl.p.conv_row_tile;
+                const LaunchSpec xspec = conv_xy_spec(pl.r_desc, 2, st, false, xa);   // sets xa.row_tile
+                const int nxy = add(xspec, xa, {g_node[o][s]});
+                nodes[nxy].xy = {pl.r_desc, 2, false, true};
                 tag(nxy, "o%d.b%d.%s", o, s, (e + 4) * (uint64_t)g.voxels());
                 ConvZArgs za{};
                 za.src = ws.TB(o, s);
@@ -726,6 +739,64 @@ cudaKernelNodeParams node_params(Node& n) {
 }
 }  // namespace
 
+namespace {
+// Tile heights of the y/x pass chosen by timing, per (dims, radius, source
+// kind, storage, sub-sampling, fused pre-blur), for the whole process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, int> g_tuned;
+
+// Time one y/x node at each candidate tile height on stream st (CUDA events,
+// one warm-up and three timed launches each) and keep the fastest in the node.
+// Its outputs are workspace intermediates the detect overwrites afterwards.
+int tune_xy_node(Node& n, int storage, cudaStream_t st, std::string* err) {
+    ConvXYArgs xa;
+    memcpy(&xa, n.arg.data(), sizeof(xa));
+    if (xa.nx > 256) return SIFT3D_OK;   // the tiled kernel for wide rows has no tile height
+    const auto key = std::make_tuple(xa.nx, xa.ny, xa.nz, n.xy.radius, n.xy.src_kind, storage, (int)n.xy.sub,
+                                     xa.dst2 != nullptr ? 1 : 0);
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) best = it->second;
+    }
+    if (best == 0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best_ms = 0.f;
+        for (int ty : {8, 16, 32}) {
+            if (e != cudaSuccess) break;
+            xa.row_tile = ty;
+            const LaunchSpec s = conv_xy_spec(n.xy.radius, n.xy.src_kind, storage, n.xy.sub, xa);
+            if (s.func == nullptr) continue;
+            void* args[1] = {&xa};
+            e = launch_spec(s, args, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_spec(s, args, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (best == 0 || ms < best_ms)) best = ty, best_ms = ms;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) {
+            if (err) *err = std::string("autotune: ") + cudaGetErrorString(e);
+            return SIFT3D_ECUDA;
+        }
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    memcpy(&xa, n.arg.data(), sizeof(xa));
+    xa.row_tile = best;
+    n.spec = conv_xy_spec(n.xy.radius, n.xy.src_kind, storage, n.xy.sub, xa);
+    n.set_args(xa);
+    return SIFT3D_OK;
+}
+}  // namespace
+
 int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, bool profile,
                cudaStream_t st, std::string* err) {
     if (ex.nodes.empty()) {
@@ -737,6 +808,19 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
                 ex.nodes.clear();
                 return SIFT3D_EINVAL;
             }
+        // tile heights of the y/x passes: timed on this device unless fixed, or
+        // unless the stream is being captured (no synchronisation allowed there)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) (void)cudaGetLastError();
+        if (ws.plan.p.autotune && ws.plan.p.conv_row_tile == 0 && cap == cudaStreamCaptureStatusNone)
+            for (auto& n : ex.nodes)
+                if (n.xy.valid) {
+                    const int rc = tune_xy_node(n, ws.plan.p.storage, st, err);
+                    if (rc != SIFT3D_OK) {
+                        ex.nodes.clear();
+                        return rc;
+                    }
+                }
         ex.cur_input = c.input;
         ex.cur_out = c.out;
         if (ex.profile) {

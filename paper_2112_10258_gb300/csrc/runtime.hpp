@@ -95,6 +95,10 @@ struct Node {
     std::string label;                     // e.g. "o0.s5.conv_z_dog"
     uint64_t algo_bytes = 0;               // minimum bytes the kernel must move
     int octave = -1;                       // octave of a pyramid / peak node (-1: sort)
+    struct XYKey {                         // a y/x pass node: what conv_xy_spec needs again
+        int radius = 0, src_kind = 0;
+        bool sub = false, valid = false;
+    } xy;
     template <class A>
     void set_args(const A& a) {
         arg.assign((sizeof(A) + 7) / 8, 0ull);

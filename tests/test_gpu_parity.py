@@ -304,3 +304,25 @@ def test_one_context_many_shapes_shares_its_arena(S):
                 det.close()
         assert got[0] == got[1], f"shape {shape}"
     shared.close()
+
+
+def test_tile_heights_and_autotune_are_bitwise_equal(S):
+    """The y/x pass's rows per CTA (8, 16, 24 or 32, or the autotuner's pick)
+    changes which CTA computes an output, never its summation: every level,
+    keypoint and descriptor is bitwise the same (also with the fused pre-blur
+    and the sub-sampling passes, and a second shape)."""
+    for shape in ((145, 174, 145), (100, 90, 80)):
+        vol = brain_like_volume(seed=12, shape=shape)
+        outs = []
+        for kw in ({"conv_row_tile": 16, "autotune": 0}, {"conv_row_tile": 8}, {"conv_row_tile": 24},
+                   {"conv_row_tile": 32}, {"autotune": 1}):
+            det, buf, n, kps = _run(S, vol, **kw)
+            brief, rrief = det.describe(buf, n)
+            lv = []
+            for o, dims in enumerate(S.plan(*shape)["dims"]):
+                for kind, idx in ((S.LEVEL_GAUSS, 4), (S.LEVEL_DOG, 2), (S.LEVEL_DESC, 2)):
+                    lv.append(det.read_level(o, kind, idx, dims).cpu().numpy().tobytes())
+            outs.append((kps.tobytes(), brief[:n].cpu().numpy().tobytes(), rrief[: n * 64].cpu().numpy().tobytes(),
+                         lv))
+            det.close()
+        assert all(o == outs[0] for o in outs[1:]), shape
