@@ -326,6 +326,34 @@ int sift3d_gaussian_blur(sift3d_ctx* ctx, const float* dev_in, int nx, int ny, i
 int sift3d_gaussian_blur_noalloc(const float* dev_in, int nx, int ny, int nz, double sigma,
                                  double trunc, float* dev_out, void* stream);
 
+/* Detect (and, with dev_brief and dev_rrief, describe) n volumes of possibly
+ * different sizes in one CUDA graph launch (no counterpart in the paper; the
+ * batched form of sift3d_detect + sift3d_describe).  Every pyramid pass (the
+ * y/x and z passes of a level, the peak test of an octave) is one persistent
+ * launch over the tiles of all volumes of a wave, so small octaves of some
+ * volumes run beside the large octaves of others; the canonical sort and the
+ * descriptors run per volume.  Results equal sift3d_detect / sift3d_describe
+ * on each volume alone, bit for bit.  Volumes are taken in waves whose
+ * workspaces fit params.hbm_budget_bytes (0: 40 GiB); the batch's device
+ * memory is held by ctx until a batch of another signature (dims, dtype,
+ * capacity, describe or not) arrives or ctx is destroyed.
+ *   dev_vols   host array of n device volume pointers (x fastest), dtype each.
+ *   dims       host array of 3n ints: nx, ny, nz of each volume.
+ *   dev_out    host array of n device arrays of capacity keypoints.
+ *   dev_brief, dev_rrief  host arrays of n device arrays (capacity words /
+ *              capacity x 64 bytes), or both NULL for detect only.
+ *   n_out      host array of n: keypoints detected per volume (may exceed
+ *              capacity; then that volume's array holds the first capacity in
+ *              canonical order), or NULL to return without waiting.
+ * Requirements: float32 storage, nx <= 256 and at least one octave for every
+ * volume, and the descriptor pre-blur of radius 4 fused into the level passes
+ * (the defaults).  Errors: SIFT3D_EINVAL (arguments, requirements),
+ * SIFT3D_ENOMEM, SIFT3D_ECAPACITY (some volume exceeded capacity; n_out
+ * complete), SIFT3D_ETIMEDOUT, SIFT3D_ECUDA. */
+int sift3d_detect_batch(sift3d_ctx* ctx, int n, const void* const* dev_vols, const int* dims, int dtype,
+                        void* stream, sift3d_keypoint* const* dev_out, int capacity,
+                        uint64_t* const* dev_brief, uint8_t* const* dev_rrief, int* n_out);
+
 /* 3D SIFT-Rank descriptors of keypoints from the last detect on ctx: the
  * paper's comparison baseline (Sec. 1 and Sec. 3.5), of which the paper fixes
  * a dominant 3x3 orientation from peaks of a discrete spherical histogram of

@@ -157,6 +157,26 @@ class Sift3D:
         self._check(rc, "sift3d_submit")
         return t
 
+    def detect_batch(self, vols, capacity: int = 16384, describe: bool = True, stream=None):
+        """Detect (and describe) a list of CUDA volumes (float32 or uint8, shapes
+        (nz, ny, nx)) in one batched graph launch.  Returns a list of
+        (keypoint_buffer, n, brief, rrief) per volume (brief/rrief None when
+        describe is False)."""
+        import torch
+        u8 = vols[0].dtype == torch.uint8
+        dims = [(v.shape[2], v.shape[1], v.shape[0]) for v in vols]
+        outs = [torch.empty(capacity * 48, dtype=torch.uint8, device="cuda") for _ in vols]
+        briefs = [torch.empty(capacity, dtype=torch.int64, device="cuda") for _ in vols] if describe else None
+        rriefs = [torch.empty(capacity * 64, dtype=torch.uint8, device="cuda") for _ in vols] if describe else None
+        rc, counts = capi.sift3d_detect_batch(self.ctx, [v.data_ptr() for v in vols], dims,
+                                              DTYPE_U8 if u8 else DTYPE_F32, _stream_handle(stream),
+                                              [o.data_ptr() for o in outs], capacity,
+                                              [b.data_ptr() for b in briefs] if describe else None,
+                                              [r.data_ptr() for r in rriefs] if describe else None)
+        self._check(rc, "sift3d_detect_batch")
+        return [(outs[i], counts[i], briefs[i] if describe else None, rriefs[i] if describe else None)
+                for i in range(len(vols))]
+
     def submit_device(self, vol) -> int:
         """Queue a CUDA tensor volume (float32 or uint8, shape (nz, ny, nx)); the
         detect reads it in place, so keep it unchanged until the request ends."""

@@ -109,6 +109,9 @@ SIGNATURES = {
                                C.c_void_p, C.c_void_p]),
     "sift3d_describe_siftrank": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sift3d_test_fail_allocation": (C.c_int, [C.c_int]),
+    "sift3d_detect_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.c_int,
+                                      C.c_void_p, C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
 }
 
 
@@ -197,6 +200,21 @@ def sift3d_gaussian_blur_noalloc(dev_in, nx, ny, nz, sigma, trunc, dev_out, stre
 
 def sift3d_read_level(ctx, octave, kind, index, dev_dst, stream) -> int:
     return _lib.sift3d_read_level(C.c_void_p(ctx), octave, kind, index, C.c_void_p(dev_dst), C.c_void_p(stream))
+
+
+def sift3d_detect_batch(ctx, vol_ptrs, dims, dtype, stream, out_ptrs, capacity, brief_ptrs=None, rrief_ptrs=None,
+                        want_counts=True):
+    """Batched detect (+ describe when brief_ptrs/rrief_ptrs are given): device
+    pointers per volume, dims as [(nx, ny, nz), ...]; returns (rc, counts)."""
+    n = len(vol_ptrs)
+    P = C.c_void_p * n
+    d = (C.c_int * (3 * n))(*[v for xyz in dims for v in xyz])
+    counts = (C.c_int * n)()
+    bp = P(*brief_ptrs) if brief_ptrs is not None else None
+    rp = P(*rrief_ptrs) if rrief_ptrs is not None else None
+    rc = _lib.sift3d_detect_batch(C.c_void_p(ctx), n, P(*vol_ptrs), d, dtype, C.c_void_p(stream), P(*out_ptrs),
+                                  capacity, bp, rp, counts if want_counts else None)
+    return rc, list(counts)
 
 
 def sift3d_test_fail_allocation(n: int) -> int:

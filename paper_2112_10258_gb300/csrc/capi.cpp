@@ -12,7 +12,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "runtime.hpp"
+#include "batch.hpp"
 
 using namespace sift3d;
 
@@ -56,6 +56,7 @@ struct sift3d_ctx {
     size_t arena_bytes = 0;
     int test_timeouts_left = 0;        // detects still to run with the peak wait test
     int* test_flag = nullptr;          // device int read by the peak kernel (test_wait_timeout > 0)
+    std::unique_ptr<BatchExec> batch;  // the last batched detect's graph and memory
 };
 
 namespace {
@@ -502,6 +503,7 @@ void sift3d_destroy(sift3d_ctx* ctx) {
     ctx->server.reset();
     if (ctx->device >= 0) cudaDeviceSynchronize();
     ctx->cache.clear();
+    ctx->batch.reset();
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->blur_scratch) cudaFree(ctx->blur_scratch);
     if (ctx->test_flag) cudaFree(ctx->test_flag);
@@ -576,6 +578,54 @@ int sift3d_describe(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, int 
     rc = enqueue_describe(ctx->last, ctx->pattern, dev_kps, n, kind, dev_brief, dev_rrief,
                           static_cast<cudaStream_t>(stream), &err);
     return rc == SIFT3D_OK ? rc : set_err(ctx, rc, err);
+}
+
+int sift3d_detect_batch(sift3d_ctx* ctx, int n, const void* const* dev_vols, const int* dims, int dtype,
+                        void* stream, sift3d_keypoint* const* dev_out, int capacity, uint64_t* const* dev_brief,
+                        uint8_t* const* dev_rrief, int* n_out) {
+    if (!ctx) return SIFT3D_EINVAL;
+    if (n < 1 || !dev_vols || !dims || !dev_out) return set_err(ctx, SIFT3D_EINVAL, "bad batch arrays");
+    if (dtype != SIFT3D_DTYPE_F32 && dtype != SIFT3D_DTYPE_U8) return set_err(ctx, SIFT3D_EINVAL, "bad dtype");
+    if (capacity < 1 || capacity > (1 << 20)) return set_err(ctx, SIFT3D_EINVAL, "capacity must be in 1..2^20");
+    if ((dev_brief == nullptr) != (dev_rrief == nullptr))
+        return set_err(ctx, SIFT3D_EINVAL, "dev_brief and dev_rrief must both be set or both be NULL");
+    const bool describe = dev_brief != nullptr;
+    std::vector<std::array<int, 3>> d(n);
+    for (int v = 0; v < n; ++v) {
+        d[v] = {dims[3 * v], dims[3 * v + 1], dims[3 * v + 2]};
+        if (!dev_vols[v] || !dev_out[v] || (describe && (!dev_brief[v] || !dev_rrief[v])))
+            return set_err(ctx, SIFT3D_EINVAL, "a batch pointer is NULL");
+        for (int a = 0; a < 3; ++a)
+            if (d[v][a] < 1 || d[v][a] > 4095) return set_err(ctx, SIFT3D_EINVAL, "each dimension must be in 1..4095");
+    }
+    int rc = ensure_device(ctx);
+    if (rc != SIFT3D_OK) return rc;
+    std::string err;
+    if (!ctx->batch || !ctx->batch->matches(d, dtype, capacity, describe)) {
+        ctx->batch.reset();   // frees the previous batch's memory (cudaFree waits for its work)
+        auto b = std::make_unique<BatchExec>();
+        rc = build_batch(ctx->p, d, dtype, capacity, describe, ctx->pattern, b.get(), &err);
+        if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
+        ctx->batch = std::move(b);
+    }
+    std::vector<uint64_t*> nb(n, nullptr);
+    std::vector<uint8_t*> nr(n, nullptr);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = run_batch(*ctx->batch, dev_vols, dev_out, describe ? dev_brief : nb.data(), describe ? dev_rrief : nr.data(),
+                   st, &err);
+    if (rc != SIFT3D_OK) return set_err(ctx, rc, err);
+    if (n_out) {
+        cudaError_t e = cudaMemcpyAsync(n_out, ctx->batch->counts, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_err(ctx, SIFT3D_ECUDA, std::string("detect_batch: ") + cudaGetErrorString(e));
+        bool over = false;
+        for (int v = 0; v < n; ++v) {
+            if (n_out[v] == -2) return set_err(ctx, SIFT3D_ETIMEDOUT, "a bounded device wait ran out (peak copy)");
+            over = over || n_out[v] > capacity;
+        }
+        if (over) return set_err(ctx, SIFT3D_ECAPACITY, "more keypoints than capacity in some volume");
+    }
+    return SIFT3D_OK;
 }
 
 int sift3d_describe_siftrank(sift3d_ctx* ctx, const sift3d_keypoint* dev_kps, int n, uint8_t* dev_desc,

@@ -106,6 +106,7 @@ struct PeakTmaArgs {   // 128-byte aligned through CUtensorMap
     int x_start;                        // x of the first tile's halo origin (multiple of 8)
     const int* test_flag;               // null, or *test_flag != 0: a CTA's first wait is one non-blocking test
     int* err;                           // set to 1 when a TMA wait runs out
+    int gx, gy, gz;                     // tiles per axis (batched launches)
 };
 
 // Tile geometry of the peak kernel for a storage type: the halo origin of the
@@ -119,6 +120,7 @@ struct SortArgs {
     const int* count;
     const int* err;             // non-zero: a bounded wait ran out, report -2
     int* count_out;             // total detected (may exceed capacity)
+    int* count_copy;            // null, or a second place for that total (batched detects)
     int capacity;
 };
 
@@ -174,6 +176,34 @@ struct ReadLevelArgs {
     float* dst;
 };
 
+// A batched launch: the per-volume argument structs of one pass and the
+// prefix sums of their work items; item i belongs to the volume v with
+// prefix[v] <= i < prefix[v + 1].
+struct BatchTable {
+    const void* args;          // device array of n per-volume argument structs
+    const int* prefix;         // device array of n + 1 item offsets
+    int n, total;              // volumes, items (= prefix[n])
+};
+
+// A batched convolution pass: every volume filters the same level, so the
+// taps travel in the kernel parameters (constant bank) with the table.
+struct BatchConv {
+    BatchTable t;
+    Taps taps, taps2;
+};
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ int batch_volume(const BatchTable& b, int item) {
+    int lo = 0, hi = b.n - 1;  // the last v with prefix[v] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(b.prefix + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+
 // A kernel launch with its single by-value argument struct, usable both for a
 // direct launch and as a CUDA graph kernel node.
 struct LaunchSpec {
@@ -182,6 +212,8 @@ struct LaunchSpec {
     size_t smem = 0;
     const char* name = "";
 };
+
+int device_sm_count();   // SMs of the current device (cached)
 
 // Launch of a spec on a stream.
 cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st);
@@ -192,8 +224,16 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYA
 LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a);
 LaunchSpec peak_spec(int storage, const PeakTmaArgs& a);
 LaunchSpec sort_spec(const SortArgs& a);
+void peak_fill_tiles(PeakTmaArgs* A);             // sets gx, gy, gz
+LaunchSpec peak_batch_spec(int ns, int total);    // batched peaks over a BatchTable of PeakTmaArgs
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
+// Batched passes over many volumes (float32 storage): persistent grids over a
+// BatchTable of per-volume arguments; *_items gives one volume's work items.
+LaunchSpec conv_xy_batch_spec(int radius, int src_kind, bool sub, bool blur, int nx_max, int row_tile, int total);
+LaunchSpec conv_z_batch_spec(int radius, bool blur, int total);
+int conv_xy_items(const ConvXYArgs& a);
+int conv_z_items(const ConvZArgs& a);
 LaunchSpec pack_spec(const PackArgs& a);
 LaunchSpec match_spec(int kind, const MatchArgs& a);
 // SIFT-Rank descriptors of keypoints on the levels of d.lv (G_s, not pre-blurred).

@@ -77,14 +77,14 @@ __device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, in
 }
 
 template <int R, typename S, int RB>
-__global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
+__device__ __forceinline__ void z_body(const ConvZArgs& a, const Taps& taps, const Taps& taps2, int pb, int zt) {
     using P = Pair<S>;
     using PT = typename P::T;
     constexpr bool narrow = sizeof(S) == 2;   // 16-bit storage: residuals travel with the levels
-    const int64_t pair = (int64_t)blockIdx.x * Z_THREADS + threadIdx.x;
+    const int64_t pair = (int64_t)pb * Z_THREADS + threadIdx.x;
     const int64_t pz2 = a.pz / 2;
     if (pair >= pz2) return;
-    const int z0 = blockIdx.y * Z_TZ;
+    const int z0 = zt * Z_TZ;
     const bool interior = z0 - R >= 0 && z0 + Z_TZ + R <= a.nz;
     const bool with_dog = a.dog != nullptr;
     float2 v[Z_TZ + 2 * R];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
         if (z0 + j >= a.nz) break;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(a.taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
+        for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
         const PT g = P::put(acc);
         *dst = g;
         if constexpr (narrow) {   // acc - stored value, exact in float32
@@ -151,10 +151,28 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
             if (z0 + j >= a.nz) break;
             float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = -RB; k <= RB; ++k) acc2 = __ffma2_rn(f2(a.taps2.w[k < 0 ? -k : k]), u[j + RB + k], acc2);
+            for (int k = -RB; k <= RB; ++k) acc2 = __ffma2_rn(f2(taps2.w[k < 0 ? -k : k]), u[j + RB + k], acc2);
             *dst2 = P::put(acc2);
             dst2 += pz2;
         }
+    }
+}
+
+template <int R, typename S, int RB>
+__global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
+    z_body<R, S, RB>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y);
+}
+
+// Batched: one flat list of (volume, column block, z tile) items.
+template <int R, typename S, int RB>
+__global__ void __launch_bounds__(Z_THREADS) conv_z_batch(const BatchConv b) {
+    const ConvZArgs* vols = static_cast<const ConvZArgs*>(b.t.args);
+    for (int item = blockIdx.x; item < b.t.total; item += gridDim.x) {
+        const int v = batch_volume(b.t, item);
+        const ConvZArgs a = vols[v];
+        const int local = item - b.t.prefix[v];
+        const int cols = (int)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS);
+        z_body<R, S, RB>(a, b.taps, b.taps2, local % cols, local / cols);
     }
 }
 
@@ -272,9 +290,9 @@ __device__ __forceinline__ void x_pass_rows(const float2* line, const Taps& taps
 // RB > 0: also filter the same source rows with the descriptor pre-blur
 // (radius RB <= R, taps2) into dst2.
 template <int R, int MODE, typename Tin, typename Tbase, int RB>
-__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
+__device__ __forceinline__ void row_body(const ConvXYArgs& a, const Taps& taps, const Taps& taps2, int yb, int z,
+                                         float2* rows_sm) {
     static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
-    extern __shared__ __align__(16) float2 rows_sm[];
     const int nx = a.nx;
     const int W = row_line(nx, R);
     constexpr int RA = row_apron(R);
@@ -282,8 +300,7 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
     const int nlines = ty / 2;                          // row-pair lines
     float2* mid = rows_sm;                              // [nlines][W]
     float2* mid2 = rows_sm + nlines * W;                // same, pre-blur (RB > 0)
-    const int y0 = blockIdx.x * ty;
-    const int z = blockIdx.y;
+    const int y0 = yb * ty;
     const int tid = threadIdx.x;
     const Tin* src = static_cast<const Tin*>(a.src);
     if (a.zero_count != nullptr && y0 == 0 && z == 0 && tid < kDetectCounters) a.zero_count[tid] = 0;
@@ -347,7 +364,7 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
             float2 e = make_float2(0.f, 0.f), f = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = -R; k <= R; ++k) {
-                const float2 w = f2(a.taps.w[k < 0 ? -k : k]);
+                const float2 w = f2(taps.w[k < 0 ? -k : k]);
                 e = __ffma2_rn(w, v[j + R + k], e);
                 f = __ffma2_rn(w, v[j + 1 + R + k], f);
             }
@@ -357,7 +374,7 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
                 f = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = -RB; k <= RB; ++k) {
-                    const float2 w = f2(a.taps2.w[k < 0 ? -k : k]);
+                    const float2 w = f2(taps2.w[k < 0 ? -k : k]);
                     e = __ffma2_rn(w, v[j + R + k], e);
                     f = __ffma2_rn(w, v[j + 1 + R + k], f);
                 }
@@ -393,9 +410,31 @@ __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArg
         if (y >= a.ny) continue;
         const int64_t off = (int64_t)z * a.pz + (int64_t)y * a.py + x0;
         const bool second = y + 1 < a.ny;
-        x_pass_rows<R, R>(mid + rp * W, a.taps, x0, a.dst + off, second ? a.dst + off + a.py : nullptr);
+        x_pass_rows<R, R>(mid + rp * W, taps, x0, a.dst + off, second ? a.dst + off + a.py : nullptr);
         if constexpr (RB > 0)
-            x_pass_rows<R, RB>(mid2 + rp * W, a.taps2, x0, a.dst2 + off, second ? a.dst2 + off + a.py : nullptr);
+            x_pass_rows<R, RB>(mid2 + rp * W, taps2, x0, a.dst2 + off, second ? a.dst2 + off + a.py : nullptr);
+    }
+}
+
+template <int R, int MODE, typename Tin, typename Tbase, int RB>
+__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
+    extern __shared__ __align__(16) float2 rows_sm[];
+    row_body<R, MODE, Tin, Tbase, RB>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y, rows_sm);
+}
+
+// Batched: the CTAs walk the tiles of every volume of the batch (grid-stride
+// over one flat tile list; a tile's volume is found in the prefix sums).
+template <int R, int MODE, typename Tin, typename Tbase, int RB>
+__global__ void __launch_bounds__(ROW_MAX_NX, 2) conv_xy_row_batch(const BatchConv b) {
+    extern __shared__ __align__(16) float2 rows_sm[];
+    const ConvXYArgs* vols = static_cast<const ConvXYArgs*>(b.t.args);
+    for (int item = blockIdx.x; item < b.t.total; item += gridDim.x) {
+        const int v = batch_volume(b.t, item);
+        const ConvXYArgs a = vols[v];   // pointers and dims; the taps come from the kernel parameters
+        const int local = item - b.t.prefix[v];
+        const int nyb = (a.ny + a.row_tile - 1) / a.row_tile;
+        row_body<R, MODE, Tin, Tbase, RB>(a, b.taps, b.taps2, local % nyb, local / nyb, rows_sm);
+        __syncthreads();   // the next tile reuses the staged rows
     }
 }
 
@@ -451,6 +490,44 @@ const void* xy_func(int r, int* smem) {
 template <int MODE, typename Tin, typename Tbase>
 const void* row_func(int r, int nx, int ty, int* smem) {
     return row_func_table<MODE, Tin, Tbase>(r, nx, ty, smem, RadiusSeq{});
+}
+
+// Batched instances: float32 storage (float32 or uint8 input).
+template <int MODE, typename Tin, int... Rs>
+const void* row_batch_table(int r, std::integer_sequence<int, Rs...>) {
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_batch<Rs + 1, MODE, Tin, float, 0>)...};
+    return fns[r - 1];
+}
+
+template <int... Rs>
+const void* row_blur_batch_table(int r, std::integer_sequence<int, Rs...>) {
+    constexpr int RB = kFusedBlurRadius;
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_batch<Rs + RB, 0, float, float, RB>)...};
+    return r < RB ? nullptr : fns[r - RB];
+}
+
+template <int... Rs>
+const void* z_batch_table(int r, std::integer_sequence<int, Rs...>) {
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_batch<Rs + 1, float, 0>)...};
+    return fns[r - 1];
+}
+
+template <int... Rs>
+const void* z_blur_batch_table(int r, std::integer_sequence<int, Rs...>) {
+    constexpr int RB = kFusedBlurRadius;
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_batch<Rs + RB, float, RB>)...};
+    return r < RB ? nullptr : fns[r - RB];
+}
+
+// A grid of at most the CTAs that fit the device at once (the kernels loop).
+dim3 persistent_grid(const void* func, int threads, size_t smem, int total) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess || per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    const int cap = per_sm * device_sm_count();
+    return dim3((unsigned)std::max(1, std::min(total, cap)));
 }
 
 }  // namespace
@@ -526,6 +603,53 @@ LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
     s.smem = 0;
     s.name = a.dst2 ? "conv_z_dog_blur" : (a.dog ? "conv_z_dog" : "conv_z");
     return s;
+}
+
+}  // namespace sift3d
+
+namespace sift3d {
+
+LaunchSpec conv_xy_batch_spec(int radius, int src_kind, bool sub, bool blur, int nx_max, int row_tile, int total) {
+    LaunchSpec s;
+    if (radius < 1 || radius > kMaxRadius || nx_max > ROW_MAX_NX) return s;
+    const int ty = row_tile;
+    if (blur) {
+        if (sub || src_kind != 2) return s;
+        s.func = row_blur_batch_table(radius, BlurRadiusSeq{});
+    } else if (sub) {
+        s.func = row_batch_table<2, float>(radius, RadiusSeq{});
+    } else if (src_kind == 0) {
+        s.func = row_batch_table<1, float>(radius, RadiusSeq{});
+    } else if (src_kind == 1) {
+        s.func = row_batch_table<1, uint8_t>(radius, RadiusSeq{});
+    } else {
+        s.func = row_batch_table<0, float>(radius, RadiusSeq{});
+    }
+    if (s.func == nullptr) return s;
+    const int smem = row_smem(nx_max, radius, blur ? kFusedBlurRadius : 0, ty);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    s.block = dim3(row_threads(nx_max, ty));
+    s.smem = smem;
+    s.grid = persistent_grid(s.func, (int)s.block.x, s.smem, total);
+    s.name = blur ? "conv_xy_blur_batch" : (sub ? "conv_xy_sub_batch" : "conv_xy_batch");
+    return s;
+}
+
+LaunchSpec conv_z_batch_spec(int radius, bool blur, int total) {
+    LaunchSpec s;
+    if (radius < 1 || radius > kMaxRadius) return s;
+    s.func = blur ? z_blur_batch_table(radius, BlurRadiusSeq{}) : z_batch_table(radius, RadiusSeq{});
+    if (s.func == nullptr) return s;
+    s.block = dim3(Z_THREADS);
+    s.grid = persistent_grid(s.func, Z_THREADS, 0, total);
+    s.name = blur ? "conv_z_dog_blur_batch" : "conv_z_dog_batch";
+    return s;
+}
+
+// Work items of one volume in a batched pass.
+int conv_xy_items(const ConvXYArgs& a) { return ((a.ny + a.row_tile - 1) / a.row_tile) * a.nz; }
+int conv_z_items(const ConvZArgs& a) {
+    return (int)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS) * ((a.nz + Z_TZ - 1) / Z_TZ);
 }
 
 }  // namespace sift3d

@@ -257,31 +257,27 @@ __device__ __noinline__ void test_overflow(const PeakArgs& a, const S* p, float 
     }
 }
 
+// One 32x8x8 tile (tile coordinates bx, by, bz) of the octave A describes,
+// staged through the CTA's barrier `bar` in the given phase parity.  Returns
+// false when the copy's wait ran out (the CTA must leave).
 template <typename S, int NS>
-__global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant__ PeakTmaArgs A) {
+__device__ __forceinline__ bool peak_tile(const PeakTmaArgs& A, int bx, int by, int bz, unsigned parity, S* sm,
+                                          uint64_t* bar_p, unsigned* surv, int* n_surv_p) {
     constexpr int NL = NS + 2;
     constexpr int BX = box_w<S>();
     constexpr int PL = SY * BX;            // one staged z plane
-    constexpr int LV = SZ * PL;            // one staged level
-    extern __shared__ __align__(128) unsigned char pk_raw[];
-    S* sm = reinterpret_cast<S*>(pk_raw);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ unsigned surv[SURV];
-    __shared__ int n_surv;
+    constexpr int LV = level_elems<S>();   // one staged level
+    uint64_t& bar = *bar_p;
+    int& n_surv = *n_surv_p;
     const PeakArgs& a = A.a;
     const int lane = threadIdx.x, w = threadIdx.y;
     const int tid = lane + TX * w;
-    const int xs = A.x_start + blockIdx.x * TX;           // halo origin of this tile
-    const int ys = a.border - 1 + blockIdx.y * TY;
-    const int zs = a.border - 1 + blockIdx.z * TZ;
+    const int xs = A.x_start + bx * TX;                   // halo origin of this tile
+    const int ys = a.border - 1 + by * TY;
+    const int zs = a.border - 1 + bz * TZ;
 
     if (tid == 0) {
         n_surv = 0;
-        tma::mbar_init(&bar, 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
         tma::mbar_expect_tx(&bar, (unsigned)(NL * LV * sizeof(S)));
         tma::load_4d(sm, &A.dogs, xs, ys, zs, 0, &bar);
     }
@@ -291,13 +287,14 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
     // bound) before the whole CTA leaves, so no copy reaches shared memory after
     // the CTA's exit.
     const bool first_test = A.test_flag != nullptr && *A.test_flag != 0;
-    const bool landed = first_test ? tma::mbar_test(&bar, 0) : tma::mbar_wait_bounded(&bar, 0, tma::kWaitPolls);
+    const bool landed =
+        first_test ? tma::mbar_test(&bar, parity) : tma::mbar_wait_bounded(&bar, parity, tma::kWaitPolls);
     if (!__syncthreads_and(landed)) {
         if (tid == 0) {
             atomicExch(A.err, 1);
-            tma::mbar_wait_bounded(&bar, 0, kDrainPolls);
+            tma::mbar_wait_bounded(&bar, parity, kDrainPolls);
         }
-        return;
+        return false;
     }
 
     const int b = a.border;
@@ -381,6 +378,48 @@ __global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant_
         const int slot = slot0 + __popc(m & ((1u << lane) - 1u));
         if (slot < a.capacity) write_keypoint<S>(a, slot, kx, ky, kz, s, ssum, c, scale, pc);
     }
+    return true;
+}
+
+template <typename S, int NS>
+__global__ void __launch_bounds__(THREADS, 3) peak_kernel(const __grid_constant__ PeakTmaArgs A) {
+    extern __shared__ __align__(128) unsigned char pk_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned surv[SURV];
+    __shared__ int n_surv;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        tma::mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    peak_tile<S, NS>(A, blockIdx.x, blockIdx.y, blockIdx.z, 0u, reinterpret_cast<S*>(pk_raw), &bar, surv, &n_surv);
+}
+
+// Batched: the CTAs walk the tiles of every volume's octave in one flat list;
+// each volume's arguments (and tensor map) come from the table in global
+// memory, and the CTA's barrier changes phase with every tile it stages.
+template <typename S, int NS>
+__global__ void __launch_bounds__(THREADS, 3) peak_batch(const BatchTable t) {
+    extern __shared__ __align__(128) unsigned char pk_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned surv[SURV];
+    __shared__ int n_surv;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        tma::mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const PeakTmaArgs* vols = static_cast<const PeakTmaArgs*>(t.args);
+    unsigned k = 0;
+    for (int item = blockIdx.x; item < t.total; item += gridDim.x, ++k) {
+        const int v = batch_volume(t, item);
+        const PeakTmaArgs& A = vols[v];
+        const int local = item - t.prefix[v];
+        if (!peak_tile<S, NS>(A, local % A.gx, (local / A.gx) % A.gy, local / (A.gx * A.gy), k & 1u,
+                              reinterpret_cast<S*>(pk_raw), &bar, surv, &n_surv))
+            return;
+        __syncthreads();   // the next tile reuses the staged levels and the list
+    }
 }
 
 // ---- canonical order ------------------------------------------------------
@@ -405,7 +444,11 @@ __global__ void __launch_bounds__(SORT_THREADS) sort_kernel(const SortArgs a) {
     __shared__ unsigned long long skeys[SORT_TILE];
     const int total = *a.count;
     const int n = min(total, a.capacity);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_out = (a.err != nullptr && *a.err != 0) ? -2 : total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int reported = (a.err != nullptr && *a.err != 0) ? -2 : total;
+        *a.count_out = reported;
+        if (a.count_copy != nullptr) *a.count_copy = reported;
+    }
     if ((int)blockIdx.x * SORT_RECORDS >= n) return;
     const int sub = threadIdx.x % SORT_LANES;
     const int i = blockIdx.x * SORT_RECORDS + threadIdx.x / SORT_LANES;
@@ -475,6 +518,38 @@ LaunchSpec peak_spec(int /*storage: DoG levels are float32 for every storage typ
     s.smem = smem;
     if (s.smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
     s.name = "peak";
+    return s;
+}
+
+void peak_fill_tiles(PeakTmaArgs* A) {
+    int x_start = 0, box_x = 0, gx = 1;
+    size_t smem = 0;
+    peak_geometry<float>(A->a, &x_start, &box_x, &gx, &smem);
+    A->gx = gx;
+    A->gy = (A->a.ny - 2 * A->a.border + TY - 1) / TY;
+    A->gz = (A->a.nz - 2 * A->a.border + TZ - 1) / TZ;
+}
+
+LaunchSpec peak_batch_spec(int ns, int total) {
+    LaunchSpec s;
+    switch (ns) {
+        case 1: s.func = reinterpret_cast<const void*>(&peak_batch<float, 1>); break;
+        case 2: s.func = reinterpret_cast<const void*>(&peak_batch<float, 2>); break;
+        case 3: s.func = reinterpret_cast<const void*>(&peak_batch<float, 3>); break;
+        case 4: s.func = reinterpret_cast<const void*>(&peak_batch<float, 4>); break;
+        case 5: s.func = reinterpret_cast<const void*>(&peak_batch<float, 5>); break;
+        default: return s;
+    }
+    s.block = dim3(TX, TY);
+    s.smem = peak_smem<float>(ns + 2);
+    if (s.smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.func, THREADS, s.smem) != cudaSuccess || per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    s.grid = dim3((unsigned)std::max(1, std::min(total, per_sm * device_sm_count())));
+    s.name = "peak_batch";
     return s;
 }
 

@@ -366,6 +366,19 @@ void free_workspace(Workspace* ws) {
     ws->base = nullptr;
 }
 
+int device_sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            (void)cudaGetLastError();
+            v = 148;   // a grid for plans built without a device (host tests)
+        }
+        return v;
+    }();
+    return n;
+}
+
 cudaError_t launch_spec(const LaunchSpec& s, void** args, cudaStream_t st) {
     return cudaLaunchKernel(s.func, s.grid, s.block, args, s.smem, st);
 }
@@ -446,6 +459,78 @@ bool make_peak_tma_args(const Workspace& ws, int o, int first_scale, int ns, Pea
     return r == CUDA_SUCCESS;
 }
 
+LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype) {
+    const Plan& pl = ws.plan;
+    const OctaveGeom& g = pl.oct[o];
+    LevelArgs la;
+    ConvXYArgs& xa = la.xy;
+    xa = ConvXYArgs{};
+    xa.dst = ws.T(o);
+    xa.py = g.py;
+    xa.pz = g.pz;
+    xa.nx = g.nx;
+    xa.ny = g.ny;
+    xa.nz = g.nz;
+    xa.src_scale = 1.0f;
+    la.src_kind = 2;
+    la.sub = false;
+    if (o == 0 && s == 0) {   // the caller's volume, blurred from sigma_in to sigma_0
+        xa.src = input;
+        xa.src_py = pl.nx;
+        xa.src_pz = (int64_t)pl.nx * pl.ny;
+        la.src_kind = dtype == SIFT3D_DTYPE_U8 ? 1 : 0;
+        xa.src_scale = dtype == SIFT3D_DTYPE_U8 ? 1.0f / 255.0f : 1.0f;
+        xa.zero_count = ws.count;
+        xa.taps = pl.t_init;
+        la.radius = pl.r_init;
+    } else if (s == 1 && o > 0) {   // sub-sample of the previous octave's level S
+        la.sub = true;
+        xa.src = ws.G(o - 1, pl.S);
+        xa.src_py = pl.oct[o - 1].py;
+        xa.src_pz = pl.oct[o - 1].pz;
+        xa.base_out = ws.G(o, 0);
+        xa.res_out = ws.Res(o);
+        xa.taps = pl.t_inc[0];
+        la.radius = pl.r_inc[0];
+    } else {
+        xa.src = ws.G(o, s - 1);
+        xa.src_py = g.py;
+        xa.src_pz = g.pz;
+        xa.taps = pl.t_inc[s - 1];
+        la.radius = pl.r_inc[s - 1];
+    }
+    // The level's own y/x pass also applies the descriptor pre-blur to its
+    // source G_{s-1} (s-1 = 1..S) when the fused variant exists.
+    la.fused_blur = pl.r_desc == kFusedBlurRadius && g.nx <= 256 && !la.sub && la.src_kind == 2 && s - 1 >= 1 &&
+                    s - 1 <= pl.S && la.radius >= kFusedBlurRadius;
+    if (la.fused_blur) {
+        xa.dst2 = ws.TB(o, s - 1);
+        xa.taps2 = pl.t_desc;
+    }
+    xa.row_tile = pl.p.conv_row_tile;
+    ConvZArgs& za = la.z;
+    za = ConvZArgs{};
+    za.src = ws.T(o);
+    za.dst = ws.G(o, s);
+    za.py = g.py;
+    za.pz = g.pz;
+    za.nx = g.nx;
+    za.ny = g.ny;
+    za.nz = g.nz;
+    za.taps = xa.taps;
+    if (s > 0) {
+        za.prev = ws.G(o, s - 1);
+        za.dog = static_cast<float*>(ws.D(o, s - 1));
+    }
+    za.res = ws.Res(o);
+    if (la.fused_blur) {
+        za.src2 = ws.TB(o, s - 1);
+        za.dst2 = ws.B(o, s - 1);
+        za.taps2 = pl.t_desc;
+    }
+    return la;
+}
+
 // ---- detect DAG ---------------------------------------------------------------
 std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* first_node, int* sort_node) {
     const Plan& pl = ws.plan;
@@ -477,54 +562,14 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         const OctaveGeom& g = pl.oct[o];
         int prev = -1;  // node that produced G_{s-1}
         for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
-            ConvXYArgs xa{};
-            xa.dst = ws.T(o);
-            xa.py = g.py;
-            xa.pz = g.pz;
-            xa.nx = g.nx;
-            xa.ny = g.ny;
-            xa.nz = g.nz;
-            xa.src_scale = 1.0f;
-            int src_kind = 2;
-            bool sub = false;
-            int radius;
+            LevelArgs la = level_args(ws, o, s, c.input, c.dtype);
+            ConvXYArgs& xa = la.xy;
+            const int src_kind = la.src_kind, radius = la.radius;
+            const bool sub = la.sub;
             std::vector<int> deps;
-            if (o == 0 && s == 0) {
-                xa.src = c.input;
-                xa.src_py = pl.nx;
-                xa.src_pz = (int64_t)pl.nx * pl.ny;
-                src_kind = c.dtype == SIFT3D_DTYPE_U8 ? 1 : 0;
-                xa.src_scale = c.dtype == SIFT3D_DTYPE_U8 ? 1.0f / 255.0f : 1.0f;
-                xa.zero_count = ws.count;
-                xa.taps = pl.t_init;
-                radius = pl.r_init;
-            } else if (s == 1 && o > 0) {
-                sub = true;
-                xa.src = ws.G(o - 1, pl.S);
-                xa.src_py = pl.oct[o - 1].py;
-                xa.src_pz = pl.oct[o - 1].pz;
-                xa.base_out = ws.G(o, 0);
-                xa.res_out = ws.Res(o);
-                xa.taps = pl.t_inc[0];
-                radius = pl.r_inc[0];
-                deps.push_back(g_node[o - 1][pl.S]);
-            } else {
-                xa.src = ws.G(o, s - 1);
-                xa.src_py = g.py;
-                xa.src_pz = g.pz;
-                xa.taps = pl.t_inc[s - 1];
-                radius = pl.r_inc[s - 1];
-                deps.push_back(prev);
-            }
-            // The level's own y/x pass also applies the descriptor pre-blur to its
-            // source G_{s-1} (s-1 = 1..S) when the fused variant exists.
-            const bool fuse_blur = pl.r_desc == kFusedBlurRadius && g.nx <= 256 && !sub && src_kind == 2 &&
-                                   s - 1 >= 1 && s - 1 <= pl.S && radius >= kFusedBlurRadius;
-            if (fuse_blur) {
-                xa.dst2 = ws.TB(o, s - 1);
-                xa.taps2 = pl.t_desc;
-                fused[o][s - 1] = true;
-            }
+            if (s == 1 && o > 0) deps.push_back(g_node[o - 1][pl.S]);
+            else if (!(o == 0 && s == 0)) deps.push_back(prev);
+            if (la.fused_blur) fused[o][s - 1] = true;
             xa.row_tile = pl.p.conv_row_tile;
             const LaunchSpec xspec = conv_xy_spec(radius, src_kind, st, sub, xa);   // sets xa.row_tile
             const int nxy = add(xspec, xa, deps);
@@ -537,25 +582,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 const uint64_t rd = (o == 0 && s == 0) ? in_e * N : (sub ? 8 * e * N : e * N);
                 tag(nxy, "o%d.s%d.%s", o, s, rd + 4 * N + (sub ? e * N : 0) + (xa.dst2 ? 4 * N : 0));
             }
-            ConvZArgs za{};
-            za.src = ws.T(o);
-            za.dst = ws.G(o, s);
-            za.py = g.py;
-            za.pz = g.pz;
-            za.nx = g.nx;
-            za.ny = g.ny;
-            za.nz = g.nz;
-            za.taps = xa.taps;
-            if (s > 0) {
-                za.prev = ws.G(o, s - 1);
-                za.dog = static_cast<float*>(ws.D(o, s - 1));
-            }
-            za.res = ws.Res(o);
-            if (xa.dst2 != nullptr) {
-                za.src2 = ws.TB(o, s - 1);
-                za.dst2 = ws.B(o, s - 1);
-                za.taps2 = pl.t_desc;
-            }
+            ConvZArgs& za = la.z;
             prev = add(conv_z_spec(radius, st, za), za, {nxy});
             {
                 const uint64_t N = (uint64_t)g.voxels();

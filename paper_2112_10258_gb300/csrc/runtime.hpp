@@ -114,6 +114,16 @@ struct DetectCall {
     int capacity;
 };
 
+// Arguments of level s of octave o (y/x pass then z pass with the DoG
+// epilogue): the sources, destinations and taps build_detect uses.
+struct LevelArgs {
+    ConvXYArgs xy;
+    ConvZArgs z;
+    int radius = 0, src_kind = 2;   // src_kind: 0 float32 input, 1 uint8 input, 2 a pyramid level
+    bool sub = false, fused_blur = false;
+};
+LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype);
+
 // Build the detect DAG (topologically ordered).  first_node / sort_node index
 // the two nodes that carry caller pointers.
 std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* first_node, int* sort_node);
