@@ -155,12 +155,12 @@ typedef struct sift3d_params {
     int32_t  autotune;           /* 1 (default): at the first detect of a
                                     volume shape (outside stream capture),
                                     time each full-row y/x pass at tile
-                                    heights of 8, 16 and 32 rows with CUDA
-                                    events and keep the fastest (cached per
-                                    process); results are bitwise the same
-                                    for every height.  0 = 16 rows.          */
-    int32_t  conv_row_tile;      /* 0 (default): as autotune says; 8, 16, 24
-                                    or 32 = rows per CTA of the y/x pass      */
+                                    heights of 8 and 16 rows with CUDA events
+                                    and keep the faster (cached per process);
+                                    results are bitwise the same for either
+                                    height.  0 = 16 rows.                    */
+    int32_t  conv_row_tile;      /* 0 (default): as autotune says; 8 or 16 =
+                                    rows per CTA of the y/x pass              */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

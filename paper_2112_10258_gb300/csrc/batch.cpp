@@ -20,6 +20,43 @@ namespace {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+XYVol xy_vol(const ConvXYArgs& a) {
+    XYVol q{};
+    q.src = a.src;
+    q.src_py = a.src_py;
+    q.src_pz = a.src_pz;
+    q.dst = a.dst;
+    q.py = a.py;
+    q.pz = a.pz;
+    q.base_out = a.base_out;
+    q.res_out = a.res_out;
+    q.zero_count = a.zero_count;
+    q.dst2 = a.dst2;
+    q.src_scale = a.src_scale;
+    q.nx = a.nx;
+    q.ny = a.ny;
+    q.nz = a.nz;
+    q.row_tile = a.row_tile;
+    return q;
+}
+
+ZVol z_vol(const ConvZArgs& a) {
+    ZVol q{};
+    q.src = a.src;
+    q.dst = a.dst;
+    q.prev = a.prev;
+    q.dog = a.dog;
+    q.res = a.res;
+    q.src2 = a.src2;
+    q.dst2 = a.dst2;
+    q.py = a.py;
+    q.pz = a.pz;
+    q.nx = a.nx;
+    q.ny = a.ny;
+    q.nz = a.nz;
+    return q;
+}
+
 int fail(std::string* err, int code, const std::string& msg) {
     if (err) *err = msg;
     return code;
@@ -63,7 +100,8 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
         slot_bytes = std::max(slot_bytes, round_up(workspace_bytes(pl, capacity), 256));
     }
     const uint64_t budget = p.hbm_budget_bytes ? p.hbm_budget_bytes : (40ull << 30);
-    bx->slots = (int)std::max<uint64_t>(1, std::min<uint64_t>(n, budget / std::max<size_t>(slot_bytes, 1)));
+    bx->slots = (int)std::max<uint64_t>(1, std::min<uint64_t>(std::min(n, kBatchVols),
+                                                                budget / std::max<size_t>(slot_bytes, 1)));
     int rc = alloc_device_zeroed(slot_bytes * (size_t)bx->slots, &bx->arena, err);
     if (rc != SIFT3D_OK) return rc;
 
@@ -136,23 +174,26 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
                                                          nx_max, 16, pxy.back());
                 if (xs.func == nullptr) return fail(err, SIFT3D_EINVAL, "no batched y/x kernel for this level");
                 const int nxy = add(xs, deps, "batch.conv_xy");
-                BatchConv bcx{};
+                BatchXY bcx{};
+                bcx.n = (int)xys.size();
+                bcx.total = pxy.back();
+                for (size_t i = 0; i < pxy.size(); ++i) bcx.prefix[i] = pxy[i];
                 bcx.taps = first.xy.taps;
                 bcx.taps2 = first.xy.taps2;
+                for (size_t i = 0; i < xys.size(); ++i) bcx.vol[i] = xy_vol(xys[i]);
                 nodes[nxy].set_args(bcx);
-                pend.push_back({nxy, put(xys.data(), xys.size() * sizeof(ConvXYArgs), 64),
-                                put(pxy.data(), pxy.size() * sizeof(int), 16), (int)xys.size(), pxy.back()});
-                if (o == 0 && s == 0)   // this table's rows hold the wave's input pointers
-                    bx->input_rows.push_back({pend.back().offset, w0, (int)xys.size()});
+                if (o == 0 && s == 0) bx->input_nodes.push_back({nxy, w0, (int)xys.size()});
                 const LaunchSpec zsp = conv_z_batch_spec(first.radius, first.fused_blur, pz.back());
                 if (zsp.func == nullptr) return fail(err, SIFT3D_EINVAL, "no batched z kernel for this level");
                 const int nz = add(zsp, {nxy}, "batch.conv_z");
-                BatchConv bcz{};
+                BatchZ bcz{};
+                bcz.n = (int)zs.size();
+                bcz.total = pz.back();
+                for (size_t i = 0; i < pz.size(); ++i) bcz.prefix[i] = pz[i];
                 bcz.taps = first.z.taps;
                 bcz.taps2 = first.z.taps2;
+                for (size_t i = 0; i < zs.size(); ++i) bcz.vol[i] = z_vol(zs[i]);
                 nodes[nz].set_args(bcz);
-                pend.push_back({nz, put(zs.data(), zs.size() * sizeof(ConvZArgs), 64),
-                                put(pz.data(), pz.size() * sizeof(int), 16), (int)zs.size(), pz.back()});
                 g_node[o][s] = nz;
             }
             if (o > 0) g_node[o][0] = g_node[o][1];
@@ -240,14 +281,7 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
         Node& nd = nodes[t.node];
         BatchTable bt{static_cast<char*>(bx->tables) + t.offset,
                       reinterpret_cast<const int*>(static_cast<char*>(bx->tables) + t.prefix), t.nvol, t.total};
-        if (nd.label == "batch.peak") {
-            nd.set_args(bt);
-        } else {
-            BatchConv bc;
-            memcpy(&bc, nd.arg.data(), sizeof(bc));
-            bc.t = bt;
-            nd.set_args(bc);
-        }
+        nd.set_args(bt);   // only the peak nodes use device tables
     }
     return SIFT3D_OK;
 }
@@ -265,17 +299,18 @@ int run_batch(BatchExec& bx, const void* const* inputs, sift3d_keypoint* const* 
             tables_dirty = true;
         }
     }
-    if (tables_dirty) {
-        for (const BatchExec::InputRows& r : bx.input_rows) {
-            ConvXYArgs* rows = reinterpret_cast<ConvXYArgs*>(bx.host_tables.data() + r.offset);
-            for (int i = 0; i < r.count; ++i) rows[i].src = bx.vols[r.first + i].input;
-        }
-        if (cudaMemcpyAsync(bx.tables, bx.host_tables.data(), bx.host_tables.size(), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess)
-            return fail(err, SIFT3D_ECUDA, "batch input table");
-    }
-    // outputs: sort and describe node parameters
+    // inputs: the first y/x node of each wave carries its volumes' pointers
     std::vector<int> changed;
+    if (tables_dirty)
+        for (const BatchExec::InputNode& r : bx.input_nodes) {
+            Node& nd = bx.nodes[r.node];
+            BatchXY bxy;
+            memcpy(&bxy, nd.arg.data(), sizeof(bxy));
+            for (int i = 0; i < r.count; ++i) bxy.vol[i].src = bx.vols[r.first + i].input;
+            nd.set_args(bxy);
+            changed.push_back(r.node);
+        }
+    // outputs: sort and describe node parameters
     for (int v = 0; v < n; ++v) {
         BatchVolume& bv = bx.vols[v];
         if (bv.sort_node < 0) continue;

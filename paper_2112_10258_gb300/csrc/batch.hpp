@@ -29,11 +29,11 @@ struct BatchExec {
     int* counts = nullptr;              // per-volume totals (inside tables)
     size_t table_bytes = 0;
     std::vector<unsigned char> host_tables;
-    struct InputRows {                  // rows of the input pass's table of one wave
-        size_t offset;
+    struct InputNode {                  // the input pass of one wave: its node and volumes
+        int node;
         int first, count;
     };
-    std::vector<InputRows> input_rows;
+    std::vector<InputNode> input_nodes;
     std::vector<BatchVolume> vols;
     std::vector<Node> nodes;
     std::vector<cudaGraphNode_t> gnodes;

@@ -185,12 +185,63 @@ struct BatchTable {
     int n, total;              // volumes, items (= prefix[n])
 };
 
-// A batched convolution pass: every volume filters the same level, so the
-// taps travel in the kernel parameters (constant bank) with the table.
-struct BatchConv {
-    BatchTable t;
-    Taps taps, taps2;
+// A batched convolution pass over at most kBatchVols volumes: every volume
+// filters the same level, so the taps are shared, and the volumes' pointers
+// and dims travel in the kernel parameters as well (uniform across a CTA, so
+// they stay in the constant bank and uniform registers).
+constexpr int kBatchVols = 64;
+
+struct XYVol {                 // the per-volume fields of ConvXYArgs
+    const void* src;
+    int64_t src_py, src_pz;
+    float* dst;
+    int64_t py, pz;
+    void* base_out;
+    __half* res_out;
+    int* zero_count;
+    float* dst2;
+    float src_scale;
+    int nx, ny, nz, row_tile;
 };
+
+struct ZVol {                  // the per-volume fields of ConvZArgs
+    const float* src;
+    void* dst;
+    const void* prev;
+    float* dog;
+    __half* res;
+    const float* src2;
+    void* dst2;
+    int64_t py, pz;
+    int nx, ny, nz;
+};
+
+struct BatchXY {
+    int n, total;
+    int prefix[kBatchVols + 1];
+    Taps taps, taps2;
+    XYVol vol[kBatchVols];
+};
+
+struct BatchZ {
+    int n, total;
+    int prefix[kBatchVols + 1];
+    Taps taps, taps2;
+    ZVol vol[kBatchVols];
+};
+// Kernel parameters are limited to 32764 bytes.
+static_assert(sizeof(BatchXY) <= 32764 && sizeof(BatchZ) <= 32764, "batch parameters too large");
+
+// The volume of item i of a parameter-embedded batch (a uniform search).
+__host__ __device__ inline int batch_param_volume(const int* prefix, int n, int item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 #if defined(__CUDACC__)
 __device__ __forceinline__ int batch_volume(const BatchTable& b, int item) {
@@ -228,8 +279,8 @@ void peak_fill_tiles(PeakTmaArgs* A);             // sets gx, gy, gz
 LaunchSpec peak_batch_spec(int ns, int total);    // batched peaks over a BatchTable of PeakTmaArgs
 LaunchSpec describe_spec(int storage, const DescribeArgs& a, int n_max);
 LaunchSpec read_level_spec(int storage, const ReadLevelArgs& a);
-// Batched passes over many volumes (float32 storage): persistent grids over a
-// BatchTable of per-volume arguments; *_items gives one volume's work items.
+// Batched passes over many volumes (float32 storage): persistent grids over
+// per-volume arguments (BatchXY / BatchZ); *_items gives one volume's work items.
 LaunchSpec conv_xy_batch_spec(int radius, int src_kind, bool sub, bool blur, int nx_max, int row_tile, int total);
 LaunchSpec conv_z_batch_spec(int radius, bool blur, int total);
 int conv_xy_items(const ConvXYArgs& a);

@@ -76,8 +76,9 @@ __device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, in
     }
 }
 
-template <int R, typename S, int RB>
-__device__ __forceinline__ void z_body(const ConvZArgs& a, const Taps& taps, const Taps& taps2, int pb, int zt) {
+// A: ConvZArgs, or the batched ZVol (the same field names, no taps).
+template <int R, typename S, int RB, class A>
+__device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps& taps2, int pb, int zt) {
     using P = Pair<S>;
     using PT = typename P::T;
     constexpr bool narrow = sizeof(S) == 2;   // 16-bit storage: residuals travel with the levels
@@ -160,19 +161,19 @@ __device__ __forceinline__ void z_body(const ConvZArgs& a, const Taps& taps, con
 
 template <int R, typename S, int RB>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
-    z_body<R, S, RB>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y);
+    z_body<R, S, RB, ConvZArgs>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y);
 }
 
 // Batched: one flat list of (volume, column block, z tile) items.
 template <int R, typename S, int RB>
-__global__ void __launch_bounds__(Z_THREADS) conv_z_batch(const BatchConv b) {
-    const ConvZArgs* vols = static_cast<const ConvZArgs*>(b.t.args);
-    for (int item = blockIdx.x; item < b.t.total; item += gridDim.x) {
-        const int v = batch_volume(b.t, item);
-        const ConvZArgs a = vols[v];
-        const int local = item - b.t.prefix[v];
+__global__ void __launch_bounds__(Z_THREADS) conv_z_batch(const __grid_constant__ BatchZ b) {
+    {
+        const int item = blockIdx.x;
+        const int v = batch_param_volume(b.prefix, b.n, item);
+        const ZVol& a = b.vol[v];   // read in place from the kernel parameters
+        const int local = item - b.prefix[v];
         const int cols = (int)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS);
-        z_body<R, S, RB>(a, b.taps, b.taps2, local % cols, local / cols);
+        z_body<R, S, RB, ZVol>(a, b.taps, b.taps2, local % cols, local / cols);
     }
 }
 
@@ -214,9 +215,9 @@ __host__ __device__ constexpr int row_smem(int nx, int R, int RB, int ty) {
     return (RB > 0 ? 2 : 1) * (ty / 2) * row_line(nx, R) * 8;
 }
 
-// Threads of a row CTA of ty rows: enough for every y task (column pair x
-// RY rows) or every x task (row pair x 8 columns) in one round, at most
-// ROW_MAX_NX; the passes loop over their tasks.
+// Threads of a row CTA of ty rows (8 or 16): enough for every y task (column
+// pair x RY rows, at most 256 for nx <= 256) in one round; the x pass loops
+// over its tasks (row pair x 8 columns).
 __host__ __device__ constexpr int row_threads(int nx, int ty) {
     const int pairs = (nx + 1) / 2, groups = (nx + 7) / 8;
     const int ytasks = pairs * (ty / RY), xtasks = (ty / 2) * groups;
@@ -240,8 +241,8 @@ __device__ __forceinline__ float sub_mean(const Tin* p, int64_t py, int64_t pz) 
 
 // Source values of columns (c, c+1) at row gy of plane z (MODE as above); the
 // second column repeats the first when c+1 is beyond the row (odd nx).
-template <int MODE, typename Tin>
-__device__ __forceinline__ float2 load_src_pair(const ConvXYArgs& a, const Tin* src, int z, int gy, int c, bool full) {
+template <int MODE, typename Tin, class A>
+__device__ __forceinline__ float2 load_src_pair(const A& a, const Tin* src, int z, int gy, int c, bool full) {
     if constexpr (MODE == 0) {
         using PT = typename Pair<Tin>::T;
         return Pair<Tin>::get(*reinterpret_cast<const PT*>(src + (int64_t)z * a.src_pz + (int64_t)gy * a.src_py + c));
@@ -289,8 +290,9 @@ __device__ __forceinline__ void x_pass_rows(const float2* line, const Taps& taps
 
 // RB > 0: also filter the same source rows with the descriptor pre-blur
 // (radius RB <= R, taps2) into dst2.
-template <int R, int MODE, typename Tin, typename Tbase, int RB>
-__device__ __forceinline__ void row_body(const ConvXYArgs& a, const Taps& taps, const Taps& taps2, int yb, int z,
+// A: ConvXYArgs, or the batched XYVol (the same field names, no taps).
+template <int R, int MODE, typename Tin, typename Tbase, int RB, class A>
+__device__ __forceinline__ void row_body(const A& a, const Taps& taps, const Taps& taps2, int yb, int z,
                                          float2* rows_sm) {
     static_assert(RB <= R, "the fused pre-blur reads inside the staged halo");
     const int nx = a.nx;
@@ -307,7 +309,8 @@ __device__ __forceinline__ void row_body(const ConvXYArgs& a, const Taps& taps, 
 
     // y pass
     const int pairs = (nx + 1) / 2;
-    for (int task = tid; task < pairs * (ty / RY); task += blockDim.x) {
+    if (tid < pairs * (ty / RY)) {   // one y task per thread (row_threads guarantees enough threads)
+        const int task = tid;
         const int h = task / pairs, p = task - h * pairs;
         const int c = 2 * p, r0 = h * RY;
         const bool full = c + 1 < nx;
@@ -342,7 +345,7 @@ __device__ __forceinline__ void row_body(const ConvXYArgs& a, const Taps& taps, 
         if (!walked) {
 #pragma unroll
             for (int t = 0; t < RY + 2 * R; ++t)
-                v[t] = load_src_pair<MODE, Tin>(a, src, z, min(max(gy0 + t, 0), a.ny - 1), c, full);
+                v[t] = load_src_pair<MODE, Tin, A>(a, src, z, min(max(gy0 + t, 0), a.ny - 1), c, full);
         }
         if constexpr (MODE == 2) {   // this CTA's own rows of the sub-sampled level are G_0
             using PB = Pair<Tbase>;
@@ -419,22 +422,21 @@ __device__ __forceinline__ void row_body(const ConvXYArgs& a, const Taps& taps, 
 template <int R, int MODE, typename Tin, typename Tbase, int RB>
 __global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_kernel(const ConvXYArgs a) {
     extern __shared__ __align__(16) float2 rows_sm[];
-    row_body<R, MODE, Tin, Tbase, RB>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y, rows_sm);
+    row_body<R, MODE, Tin, Tbase, RB, ConvXYArgs>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y, rows_sm);
 }
 
 // Batched: the CTAs walk the tiles of every volume of the batch (grid-stride
 // over one flat tile list; a tile's volume is found in the prefix sums).
 template <int R, int MODE, typename Tin, typename Tbase, int RB>
-__global__ void __launch_bounds__(ROW_MAX_NX, 2) conv_xy_row_batch(const BatchConv b) {
+__global__ void __launch_bounds__(ROW_MAX_NX) conv_xy_row_batch(const __grid_constant__ BatchXY b) {
     extern __shared__ __align__(16) float2 rows_sm[];
-    const ConvXYArgs* vols = static_cast<const ConvXYArgs*>(b.t.args);
-    for (int item = blockIdx.x; item < b.t.total; item += gridDim.x) {
-        const int v = batch_volume(b.t, item);
-        const ConvXYArgs a = vols[v];   // pointers and dims; the taps come from the kernel parameters
-        const int local = item - b.t.prefix[v];
+    {
+        const int item = blockIdx.x;
+        const int v = batch_param_volume(b.prefix, b.n, item);
+        const XYVol& a = b.vol[v];   // read in place from the kernel parameters
+        const int local = item - b.prefix[v];
         const int nyb = (a.ny + a.row_tile - 1) / a.row_tile;
-        row_body<R, MODE, Tin, Tbase, RB>(a, b.taps, b.taps2, local % nyb, local / nyb, rows_sm);
-        __syncthreads();   // the next tile reuses the staged rows
+        row_body<R, MODE, Tin, Tbase, RB, XYVol>(a, b.taps, b.taps2, local % nyb, local / nyb, rows_sm);
     }
 }
 
@@ -519,16 +521,6 @@ const void* z_blur_batch_table(int r, std::integer_sequence<int, Rs...>) {
     return r < RB ? nullptr : fns[r - RB];
 }
 
-// A grid of at most the CTAs that fit the device at once (the kernels loop).
-dim3 persistent_grid(const void* func, int threads, size_t smem, int total) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess || per_sm < 1) {
-        (void)cudaGetLastError();
-        per_sm = 1;
-    }
-    const int cap = per_sm * device_sm_count();
-    return dim3((unsigned)std::max(1, std::min(total, cap)));
-}
 
 }  // namespace
 
@@ -536,7 +528,7 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYA
     LaunchSpec s;
     int smem = 0;
     if (radius < 1 || radius > kMaxRadius) return s;
-    if (a.row_tile < RY || a.row_tile % RY != 0 || a.row_tile > 64) a.row_tile = ROW_TY;
+    if (a.row_tile != 8 && a.row_tile != 16) a.row_tile = ROW_TY;
     const int ty = a.row_tile;
     if (a.dst2 != nullptr) {   // level pass with the descriptor pre-blur fused in
         if (sub || src_kind != 2 || a.nx > ROW_MAX_NX) return s;
@@ -630,7 +622,7 @@ LaunchSpec conv_xy_batch_spec(int radius, int src_kind, bool sub, bool blur, int
     if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     s.block = dim3(row_threads(nx_max, ty));
     s.smem = smem;
-    s.grid = persistent_grid(s.func, (int)s.block.x, s.smem, total);
+    s.grid = dim3((unsigned)std::max(1, total));   // one tile per CTA
     s.name = blur ? "conv_xy_blur_batch" : (sub ? "conv_xy_sub_batch" : "conv_xy_batch");
     return s;
 }
@@ -641,7 +633,7 @@ LaunchSpec conv_z_batch_spec(int radius, bool blur, int total) {
     s.func = blur ? z_blur_batch_table(radius, BlurRadiusSeq{}) : z_batch_table(radius, RadiusSeq{});
     if (s.func == nullptr) return s;
     s.block = dim3(Z_THREADS);
-    s.grid = persistent_grid(s.func, Z_THREADS, 0, total);
+    s.grid = dim3((unsigned)std::max(1, total));   // one tile per CTA
     s.name = blur ? "conv_z_dog_blur_batch" : "conv_z_dog_batch";
     return s;
 }

@@ -79,9 +79,8 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.refine < 0 || p.refine > 1) return fail(err, "refine must be 0 or 1");
     if (p.test_wait_timeout < 0 || p.test_wait_timeout > 1000) return fail(err, "test_wait_timeout must be in 0..1000");
     if (p.autotune < 0 || p.autotune > 1) return fail(err, "autotune must be 0 or 1");
-    if (p.conv_row_tile != 0 && p.conv_row_tile != 8 && p.conv_row_tile != 16 && p.conv_row_tile != 24 &&
-        p.conv_row_tile != 32)
-        return fail(err, "conv_row_tile must be 0, 8, 16, 24 or 32");
+    if (p.conv_row_tile != 0 && p.conv_row_tile != 8 && p.conv_row_tile != 16)
+        return fail(err, "conv_row_tile must be 0, 8 or 16");
 
     // filter radii of the schedule
     const int S = p.scales_per_octave;
@@ -792,7 +791,7 @@ int tune_xy_node(Node& n, int storage, cudaStream_t st, std::string* err) {
         cudaError_t e = cudaEventCreate(&e0);
         if (e == cudaSuccess) e = cudaEventCreate(&e1);
         float best_ms = 0.f;
-        for (int ty : {8, 16, 32}) {
+        for (int ty : {8, 16}) {
             if (e != cudaSuccess) break;
             xa.row_tile = ty;
             const LaunchSpec s = conv_xy_spec(n.xy.radius, n.xy.src_kind, storage, n.xy.sub, xa);
