@@ -165,6 +165,19 @@ def _oracle_step(_):
     return t0, time.perf_counter()
 
 
+def _oracle_step_keys(_):
+    """_oracle_step, plus the oracle's keypoint keys (octave, scale, z, y, x) and
+    the voxels it flags as near ties."""
+    from oracle import sift3d_oracle as O
+    p = O.Params()
+    t0 = time.perf_counter()
+    r = O.detect(_ORACLE_VOL, p)
+    O.describe(r.pyramid, r.keypoints, p)
+    t1 = time.perf_counter()
+    keys = {(int(k["octave"]), int(k["scale"]), int(k["iz"]), int(k["iy"]), int(k["ix"])) for k in r.keypoints}
+    return t0, t1, keys, set(r.uncertain)
+
+
 def _oracle_pool(vol, cores):
     import multiprocessing as mp
     return mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init, initargs=(vol,))
@@ -199,13 +212,20 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
-def cpu_baseline(vol):
+def cpu_baseline(vol, gpu_keys=None):
     """The FP64 oracle on the full headline volume: one process (one core), then
-    one process per host core on the same volume started together (all cores)."""
+    one process per host core on the same volume started together (all cores).
+    With gpu_keys, the single-core run's keypoints are also compared with the
+    CUDA path's: differences outside the oracle's near ties are reported."""
     cores = _cpu_workers()
     with _oracle_pool(vol, 1) as pool:
-        t0, t1 = pool.map(_oracle_step, [0])[0]
+        t0, t1, okeys, unc = pool.map(_oracle_step_keys, [0])[0]
     single = vol.size / (t1 - t0)
+    parity = None
+    if gpu_keys is not None:
+        diff = gpu_keys ^ okeys
+        parity = {"oracle_keypoints": len(okeys), "near_ties_flagged": len(unc), "cuda_keypoints": len(gpu_keys),
+                  "differ": len(diff), "differ_outside_near_ties": len(diff - unc)}
     with _oracle_pool(vol, cores) as pool:
         spans = pool.map(_oracle_step, range(cores), chunksize=1)
     wall = max(e for _, e in spans) - min(b for b, _ in spans)
@@ -214,7 +234,8 @@ def cpu_baseline(vol):
             "sample": f"{cores} concurrent oracle runs (one process each) of the full 145x174x145 volume, detect + "
                       f"BRIEF + RRIEF, numpy float64",
             "seconds": wall,
-            "single_core": {"value": single, "unit": UNIT, "cores": 1, "seconds": t1 - t0}}
+            "single_core": {"value": single, "unit": UNIT, "cores": 1, "seconds": t1 - t0},
+            "keypoint_parity": parity}
 
 
 def kernel_source_hash():
@@ -567,6 +588,7 @@ def main():
     rriefs = [torch.empty(CAPACITY * 64, dtype=torch.uint8, device="cuda") for _ in range(P)]
     kbuf, brief, rrief = kbufs[0], briefs[0], rriefs[0]
     _, n_kp = det.detect(d_vol, capacity=CAPACITY, out=kbuf)   # also builds the graph
+    kbuf_first = kbuf.clone()
 
     def step():
         det.detect(d_vol, capacity=CAPACITY, out=kbuf, sync=False)
@@ -739,7 +761,9 @@ def main():
         return
     base = None
     if world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(vol)
+        kp = S.keypoints_to_numpy(kbuf_first, n_kp)
+        gpu_keys = {(int(k["octave"]), int(k["scale"]), int(k["iz"]), int(k["iy"]), int(k["ix"])) for k in kp}
+        base = cpu_baseline(vol, gpu_keys if args.storage == "f32" else None)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -593,23 +593,18 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             g_node[o][s] = prev;
         }
         if (o > 0) g_node[o][0] = g_node[o][1];
-        // peak detection on D_1..D_S.  Octave 0 tests each scale s in its own
-        // launch as soon as D_{s+1} exists (after level s+2), so scales 1..S-1
-        // overlap the remaining level passes; the smaller octaves test all
-        // scales in one launch after their last level.
+        // peak detection on D_1..D_S: one launch per octave after its last level
+        // (one launch per scale, each as soon as its DoG levels exist, reads
+        // every DoG level up to three times and measured slower: 0.309 against
+        // 0.286 ms per detect + describe of 145x174x145)
         if (g.nx - 2 * pl.p.border >= 1 && g.ny - 2 * pl.p.border >= 1 && g.nz - 2 * pl.p.border >= 1) {
-            const bool per_scale = o == 0 && pl.S > 1;
-            for (int s0 = 1; s0 <= pl.S; s0 += per_scale ? 1 : pl.S) {
-                const int ns = per_scale ? 1 : pl.S;
-                PeakTmaArgs pa;
-                LaunchSpec ps;
-                if (make_peak_tma_args(ws, o, s0, ns, &pa)) ps = peak_spec(st, pa);
-                else ps.name = "peak (DoG tensor map)";
-                peak_nodes.push_back(add(ps, pa, {g_node[o][s0 + ns + 1]}));
-                // the 80-neighbour test reads its ns + 2 DoG levels in full
-                tag(peak_nodes.back(), per_scale ? "o%d.d%d.%s" : "o%d.d1-%d.%s", o, per_scale ? s0 : pl.S,
-                    (uint64_t)(ns + 2) * ed * (uint64_t)g.voxels());
-            }
+            PeakTmaArgs pa;
+            LaunchSpec ps;
+            if (make_peak_tma_args(ws, o, 1, pl.S, &pa)) ps = peak_spec(st, pa);
+            else ps.name = "peak (DoG tensor map)";
+            peak_nodes.push_back(add(ps, pa, {g_node[o][pl.S + 2]}));
+            // the 80-neighbour test reads the S + 2 DoG levels in full
+            tag(peak_nodes.back(), "o%d.d1-%d.%s", o, pl.S, (uint64_t)(pl.S + 2) * ed * (uint64_t)g.voxels());
         }
         // pre-blur of G_1..G_S for the descriptors (Sec. 2.2.3), where no level
         // pass fused it
