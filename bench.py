@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--only", choices=["all", "detect"], default="all",
                     help="detect: time only the headline phase (for ncu captures)")
     ap.add_argument("--eager", action="store_true", help="direct launches instead of the CUDA graph")
+    ap.add_argument("--row-tile", type=int, choices=[0, 8, 16], default=0,
+                    help="y/x pass rows per CTA: 0 = autotuned at the first detect; 8 or 16 = fixed, no "
+                         "tuning launches (for ncu captures of a known launch order)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="volumes processed concurrently (separate contexts/streams, distinct inputs)")
     ap.add_argument("--mode", choices=["headline", "batched", "serving", "match"], default="headline",
@@ -581,7 +584,8 @@ def main():
     # ---- phase 1: the full hot path (detect + describe), graph launch path
     use_graphs = 0 if args.eager else 1
     P = max(1, args.inflight)
-    dets = [S.Sift3D(storage=storage, use_graphs=use_graphs) for _ in range(P)]
+    tile_kw = {"conv_row_tile": args.row_tile, "autotune": 0} if args.row_tile else {}
+    dets = [S.Sift3D(storage=storage, use_graphs=use_graphs, **tile_kw) for _ in range(P)]
     det = dets[0]
     kbufs = [torch.empty(CAPACITY * 48, dtype=torch.uint8, device="cuda") for _ in range(P)]
     briefs = [torch.empty(CAPACITY, dtype=torch.int64, device="cuda") for _ in range(P)]
@@ -666,8 +670,10 @@ def main():
     path_gbs = pl["algorithmic_bytes"] / (path_ms / 1e3) / 1e9
     det_path.close()
 
-    # ---- phase 3: per-kernel events inside the same graph (profile build)
-    det_prof = S.Sift3D(storage=storage, profile=1)
+    # ---- phase 3: per-kernel events around direct launches of the same
+    # kernels in the graph's order, one stream, so no concurrent branch adds
+    # to a kernel's duration
+    det_prof = S.Sift3D(storage=storage, profile=1, use_graphs=0)
     det_prof.detect(d_vol, capacity=CAPACITY, out=kbuf)
     acc = {}
     for i in range(args.warmup + args.steps):

@@ -346,8 +346,9 @@ int sift3d_gaussian_blur_noalloc(const float* dev_in, int nx, int ny, int nz, do
  *              capacity; then that volume's array holds the first capacity in
  *              canonical order), or NULL to return without waiting.
  * Requirements: float32 storage, nx <= 256 and at least one octave for every
- * volume, and the descriptor pre-blur of radius 4 fused into the level passes
- * (the defaults).  Errors: SIFT3D_EINVAL (arguments, requirements),
+ * volume.  The descriptor pre-blur rides on the level passes where its radius
+ * is 4 and every level's radius is at least 4 (the defaults), else it runs as
+ * separate batched passes.  Errors: SIFT3D_EINVAL (arguments, requirements),
  * SIFT3D_ENOMEM, SIFT3D_ECAPACITY (some volume exceeded capacity; n_out
  * complete), SIFT3D_ETIMEDOUT, SIFT3D_ECUDA. */
 int sift3d_detect_batch(sift3d_ctx* ctx, int n, const void* const* dev_vols, const int* dims, int dtype,

@@ -23,6 +23,7 @@ struct BatchExec {
     std::vector<std::array<int, 3>> dims;
     int dtype = 0, capacity = 0;
     bool describe = false;
+    bool fuse_blur = true;             // descriptor pre-blur carried by the level passes
     int slots = 0;                      // volumes per wave
     char* arena = nullptr;              // slots x the largest workspace
     void* tables = nullptr;             // device copy of host_tables

@@ -88,6 +88,7 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
     const int z0 = zt * Z_TZ;
     const bool interior = z0 - R >= 0 && z0 + Z_TZ + R <= a.nz;
     const bool with_dog = a.dog != nullptr;
+    const bool with_res = a.res != nullptr;   // 16-bit storage of a level (null: descriptor pre-blur)
     float2 v[Z_TZ + 2 * R];
     load_z_window<Z_TZ + 2 * R, R>(reinterpret_cast<const float2*>(a.src) + pair, pz2, z0, a.nz, interior, v);
     // G_{s-1} as computed, before its rounding to storage: the stored value plus
@@ -133,9 +134,11 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
         for (int k = -R; k <= R; ++k) acc = __ffma2_rn(f2(taps.w[k < 0 ? -k : k]), v[j + R + k], acc);
         const PT g = P::put(acc);
         *dst = g;
-        if constexpr (narrow) {   // acc - stored value, exact in float32
-            const float2 gs = P::get(g);
-            *rout = __floats2half2_rn(acc.x - gs.x, acc.y - gs.y);
+        if constexpr (narrow) {   // acc - stored value, exact in float32 (levels only: the
+            if (with_res) {       // descriptor pre-blur keeps no residual)
+                const float2 gs = P::get(g);
+                *rout = __floats2half2_rn(acc.x - gs.x, acc.y - gs.y);
+            }
         }
         if (with_dog) *dog = make_float2(pv[j].x - acc.x, pv[j].y - acc.y);
         dst += pz2;
@@ -456,28 +459,10 @@ const void* row_func_table(int r, int nx, int ty, int* smem, std::integer_sequen
     return fns[r - 1];
 }
 
-// Fused pre-blur variants exist for radii >= kFusedBlurRadius (index r-RB).
-template <typename Tin, int... Rs>
-const void* row_blur_func_table(int r, int nx, int ty, int* smem, std::integer_sequence<int, Rs...>) {
-    constexpr int RB = kFusedBlurRadius;
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_xy_row_kernel<Rs + RB, 0, Tin, float, RB>)...};
-    if (r < RB) return nullptr;
-    *smem = row_smem(nx, r, RB, ty);
-    return fns[r - RB];
-}
-
 template <typename S, int... Rs>
 const void* z_func_table(int r, std::integer_sequence<int, Rs...>) {
     const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, S, 0>)...};
     return fns[r - 1];
-}
-
-template <typename S, int... Rs>
-const void* z_blur_func_table(int r, std::integer_sequence<int, Rs...>) {
-    constexpr int RB = kFusedBlurRadius;
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + RB, S, RB>)...};
-    if (r < RB) return nullptr;
-    return fns[r - RB];
 }
 
 using BlurRadiusSeq = std::make_integer_sequence<int, kMaxRadius - kFusedBlurRadius + 1>;
@@ -530,19 +515,7 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYA
     if (radius < 1 || radius > kMaxRadius) return s;
     if (a.row_tile != 8 && a.row_tile != 16) a.row_tile = ROW_TY;
     const int ty = a.row_tile;
-    if (a.dst2 != nullptr) {   // level pass with the descriptor pre-blur fused in
-        if (sub || src_kind != 2 || a.nx > ROW_MAX_NX) return s;
-        if (storage == SIFT3D_STORAGE_F32) s.func = row_blur_func_table<float>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
-        else if (storage == SIFT3D_STORAGE_F16) s.func = row_blur_func_table<__half>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
-        else s.func = row_blur_func_table<__nv_bfloat16>(radius, a.nx, ty, &smem, BlurRadiusSeq{});
-        if (s.func == nullptr) return s;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(s.func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        s.grid = dim3((a.ny + ty - 1) / ty, a.nz, 1);
-        s.block = dim3(row_threads(a.nx, ty));
-        s.smem = smem;
-        s.name = "conv_xy_blur";
-        return s;
-    }
+    if (a.dst2 != nullptr) return s;   // the fused descriptor pre-blur exists in the batched kernels only
     if (a.nx <= ROW_MAX_NX) {
         if (!sub) {
             if (src_kind == 0) s.func = row_func<1, float, float>(radius, a.nx, ty, &smem);
@@ -583,17 +556,14 @@ LaunchSpec conv_xy_spec(int radius, int src_kind, int storage, bool sub, ConvXYA
 LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
     LaunchSpec s;
     if (radius < 1 || radius > kMaxRadius) return s;
-    if (a.dst2 != nullptr) {
-        if (storage == SIFT3D_STORAGE_F32) s.func = z_blur_func_table<float>(radius, BlurRadiusSeq{});
-        else if (storage == SIFT3D_STORAGE_F16) s.func = z_blur_func_table<__half>(radius, BlurRadiusSeq{});
-        else s.func = z_blur_func_table<__nv_bfloat16>(radius, BlurRadiusSeq{});
-    } else if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
+    if (a.dst2 != nullptr) return s;   // the fused descriptor pre-blur exists in the batched kernels only
+    if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
     else if (storage == SIFT3D_STORAGE_F16) s.func = z_func_table<__half>(radius, RadiusSeq{});
     else s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
     s.grid = dim3((unsigned)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
     s.block = dim3(Z_THREADS);
     s.smem = 0;
-    s.name = a.dst2 ? "conv_z_dog_blur" : (a.dog ? "conv_z_dog" : "conv_z");
+    s.name = a.dog ? "conv_z_dog" : "conv_z";
     return s;
 }
 

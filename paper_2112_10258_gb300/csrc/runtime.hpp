@@ -115,14 +115,17 @@ struct DetectCall {
 };
 
 // Arguments of level s of octave o (y/x pass then z pass with the DoG
-// epilogue): the sources, destinations and taps build_detect uses.
+// epilogue): the sources, destinations and taps.  fuse_blur: the level passes
+// also produce the descriptor pre-blur of G_{s-1} where a fused variant exists
+// (the batched path); the single-volume detect runs the pre-blur as separate
+// passes on their own graph branches, off the octave chain.
 struct LevelArgs {
     ConvXYArgs xy;
     ConvZArgs z;
     int radius = 0, src_kind = 2;   // src_kind: 0 float32 input, 1 uint8 input, 2 a pyramid level
     bool sub = false, fused_blur = false;
 };
-LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype);
+LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype, bool fuse_blur);
 
 // Build the detect DAG (topologically ordered).  first_node / sort_node index
 // the two nodes that carry caller pointers.

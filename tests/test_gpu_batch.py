@@ -24,8 +24,8 @@ def S():
     return S
 
 
-def _single(S, d, capacity):
-    det = S.Sift3D()
+def _single(S, d, capacity, **kw):
+    det = S.Sift3D(**kw)
     buf, n = det.detect(d, capacity=capacity)
     brief, rrief = det.describe(buf, n)
     out = (S.keypoints_to_numpy(buf, n).tobytes(), brief[:n].cpu().numpy().tobytes(),
@@ -50,6 +50,23 @@ def test_batch_equals_single_volume_path(S, budget_gib, u8):
             got = (S.keypoints_to_numpy(buf, n).tobytes(), brief[:n].cpu().numpy().tobytes(),
                    rrief[: n * 64].cpu().numpy().tobytes())
             assert n > 0 and got == want[i], f"volume {i} {SHAPES[i]} (call {rep})"
+    det.close()
+
+
+def test_batch_separate_preblur_equals_single_volume_path(S):
+    """A descriptor pre-blur of radius 5 (sigma 1.2) cannot ride on the level
+    passes, so the batch runs it as separate passes."""
+    vols = [brain_like_volume(seed=50 + i, shape=s) for i, s in enumerate(SHAPES[:3])]
+    dev = [torch.from_numpy(v).cuda() for v in vols]
+    cap = 8192
+    want = [_single(S, d, cap, desc_blur_sigma=1.2) for d in dev]
+    det = S.Sift3D(desc_blur_sigma=1.2)
+    res = det.detect_batch(dev, capacity=cap)
+    torch.cuda.synchronize()
+    for i, (buf, n, brief, rrief) in enumerate(res):
+        got = (S.keypoints_to_numpy(buf, n).tobytes(), brief[:n].cpu().numpy().tobytes(),
+               rrief[: n * 64].cpu().numpy().tobytes())
+        assert n > 0 and got == want[i], f"volume {i} {SHAPES[i]}"
     det.close()
 
 
