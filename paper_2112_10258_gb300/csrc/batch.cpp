@@ -201,9 +201,7 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
             }
             if (o > 0) g_node[o][0] = g_node[o][1];
             // peaks: one launch per octave over all scales
-            const bool per_scale = false;
-            for (int s0 = 1; s0 <= S; s0 += per_scale ? 1 : S) {
-                const int ns = per_scale ? 1 : S;
+            {
                 std::vector<PeakTmaArgs> pks;
                 std::vector<int> pp{0};
                 for (int v : in_o) {
@@ -212,19 +210,20 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
                     if (g.nx - 2 * pl.p.border < 1 || g.ny - 2 * pl.p.border < 1 || g.nz - 2 * pl.p.border < 1)
                         continue;
                     PeakTmaArgs pa;
-                    if (!make_peak_tma_args(bx->vols[v].ws, o, s0, ns, &pa))
+                    if (!make_peak_tma_args(bx->vols[v].ws, o, 1, S, &pa))
                         return fail(err, SIFT3D_ECUDA, "DoG tensor map");
                     peak_fill_tiles(&pa);
                     pks.push_back(pa);
                     pp.push_back(pp.back() + pa.gx * pa.gy * pa.gz);
                 }
-                if (pks.empty()) continue;
-                const LaunchSpec ps = peak_batch_spec(ns, pp.back());
-                if (ps.func == nullptr) return fail(err, SIFT3D_EINVAL, "no batched peak kernel");
-                const int np = add(ps, {g_node[o][s0 + ns + 1]}, "batch.peak");
-                pend.push_back({np, put(pks.data(), pks.size() * sizeof(PeakTmaArgs), 128),
-                                put(pp.data(), pp.size() * sizeof(int), 16), (int)pks.size(), pp.back()});
-                peak_nodes.push_back(np);
+                if (!pks.empty()) {
+                    const LaunchSpec ps = peak_batch_spec(S, pp.back());
+                    if (ps.func == nullptr) return fail(err, SIFT3D_EINVAL, "no batched peak kernel");
+                    const int np = add(ps, {g_node[o][S + 2]}, "batch.peak");
+                    pend.push_back({np, put(pks.data(), pks.size() * sizeof(PeakTmaArgs), 128),
+                                    put(pp.data(), pp.size() * sizeof(int), 16), (int)pks.size(), pp.back()});
+                    peak_nodes.push_back(np);
+                }
             }
             // descriptor pre-blur of G_1..G_S (Sec. 2.2.3): a y/x and a z pass per
             // level over the wave, beside the octave chain

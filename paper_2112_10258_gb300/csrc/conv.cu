@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(Z_THREADS) conv_z_batch(const __grid_constant_
 //         (Sec. 2.2.2 "Sub-sampling"), and the CTA's own rows of the means are
 //         written to base_out as the octave's G_0.
 constexpr int RY = 8;                 // rows per y task
-constexpr int ROW_TY = 2 * RY;        // default rows per CTA (ConvXYArgs.row_tile: a multiple of RY)
+constexpr int ROW_TY = 2 * RY;        // default rows per CTA (ConvXYArgs.row_tile: 8 or 16)
 
 __host__ __device__ constexpr int row_apron(int R) { return R + (R & 1); }
 
@@ -301,8 +301,9 @@ __device__ __forceinline__ void row_body(const A& a, const Taps& taps, const Tap
     const int nx = a.nx;
     const int W = row_line(nx, R);
     constexpr int RA = row_apron(R);
-    const int ty = a.row_tile;                          // rows of this CTA (multiple of RY)
-    const int nlines = ty / 2;                          // row-pair lines
+    const int ty = a.row_tile;                          // rows of this CTA: 8 or 16
+    const int lg_lines = ty == 16 ? 3 : 2;              // log2 of the row-pair lines (no divisions below)
+    const int nlines = 1 << lg_lines;
     float2* mid = rows_sm;                              // [nlines][W]
     float2* mid2 = rows_sm + nlines * W;                // same, pre-blur (RB > 0)
     const int y0 = yb * ty;
@@ -397,7 +398,7 @@ __device__ __forceinline__ void row_body(const A& a, const Taps& taps, const Tap
         const int nb = RB > 0 ? 2 : 1;
         const int lane = tid & 31, nwarps = blockDim.x >> 5;   // blockDim.x is a multiple of 32
         for (int l = tid >> 5; l < nb * nlines; l += nwarps) {   // a warp per line
-            float2* line = (l < nlines ? mid : mid2) + (l % nlines) * W;
+            float2* line = (l < nlines ? mid : mid2) + (l & (nlines - 1)) * W;
             for (int e = lane; e < per_line; e += 32) {
                 if (e < RA) line[e] = line[RA];
                 else line[RA + nx + (e - RA)] = line[RA + nx - 1];
@@ -409,8 +410,8 @@ __device__ __forceinline__ void row_body(const A& a, const Taps& taps, const Tap
     // x pass
     const int groups = (nx + ROW_J - 1) / ROW_J;
     for (int item = tid; item < nlines * groups; item += blockDim.x) {
-        const int rp = item % nlines;
-        const int g = item / nlines;
+        const int rp = item & (nlines - 1);
+        const int g = item >> lg_lines;
         const int x0 = g * ROW_J;
         const int y = y0 + 2 * rp;
         if (y >= a.ny) continue;

@@ -103,6 +103,24 @@ def test_blob_case_64cubed_keypoints_and_descriptors(S):
     det.close()
 
 
+@pytest.mark.parametrize("blur", [0.0, 0.5, 1.5, 2.5])
+def test_descriptor_preblur_sweep(S, blur):
+    """The descriptor pre-blur sigma of Sec. 2.2.3's study (0: sample G_s
+    directly; 0.5, 1.5, 2.5: radii 2, 6, 10 of the separate pre-blur passes):
+    every pre-blurred level within 1e-5 of the oracle's, bits and ranks equal
+    up to flagged near ties."""
+    vol = blob_volume(seed=5, shape=(50, 46, 42), n_blobs=20)
+    det, buf, n, kps = _run(S, vol, desc_blur_sigma=blur)
+    p = _oracle_params(desc_blur_sigma=blur)
+    ref = O.detect(vol, p)
+    _check_levels(S, det, ref, p)
+    compare_keypoints(kps, ref)
+    assert n > 0
+    dexc = _check_descriptors(S, det, buf, n, kps, ref, p)
+    assert dexc <= max(2, n // 10)
+    det.close()
+
+
 @pytest.mark.parametrize("method", [1, 2, 4, 5])
 def test_descriptor_point_selection_methods(S, method):
     """Sec. 2.2.3 point-selection methods 1, 2, 4 and 5 (method 3 is the default
