@@ -726,8 +726,10 @@ def main():
     # ---- phase 4: end to end through the public serving API with host buffers
     e2e = None
     if not args.no_e2e:
-        srv = S.Sift3D(storage=storage, max_inflight=4, max_keypoints=8192)
-        pool = [torch.from_numpy(np.ascontiguousarray(np.roll(vol, 7 * i, axis=2))).pin_memory() for i in range(4)]
+        depth = 8   # requests in flight
+        srv = S.Sift3D(storage=storage, max_inflight=depth, max_keypoints=8192)
+        pool = [torch.from_numpy(np.ascontiguousarray(np.roll(vol, 7 * i, axis=2))).pin_memory()
+                for i in range(depth)]
         def wait(t, deadline):
             while srv.poll(t, 100000, copy=False) is None:
                 if time.monotonic() > deadline:
@@ -741,11 +743,11 @@ def main():
             for k in range(K):
                 h = pool[k % len(pool)]
                 q.append(srv.submit_ptr(h.data_ptr(), S.DTYPE_F32, SHAPE, flags=S.SUBMIT_NOCOPY))
-                while len(q) >= 4:
+                while len(q) >= depth:
                     wait(q.popleft(), deadline)
             while q:
                 wait(q.popleft(), deadline)
-        run_e2e(max(args.warmup, 4))
+        run_e2e(max(args.warmup, 2 * depth))
         barrier()
         t0 = time.perf_counter()
         run_e2e(args.steps)
@@ -755,7 +757,7 @@ def main():
                "d2h_bytes_per_step": int(4 + n_kp * (48 + 8 + 64)),
                "ms_per_step": 1e3 * t_e2e / args.steps,
                "path": "sift3d_submit (pinned host volume, NOCOPY) -> H2D, detect, describe, count + records "
-                       "into mapped host memory -> sift3d_poll; 4 requests in flight"}
+                       f"into mapped host memory -> sift3d_poll; {depth} requests in flight"}
         srv.close()
 
     for d_ in dets:

@@ -1,5 +1,6 @@
 // extern "C" entry points of include/sift3d.h and the serving scheduler.
 #include <chrono>
+#include <atomic>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -221,6 +222,17 @@ struct Server {
     uint64_t budget = 0, used = 0, pooled = 0;
     bool stop = false;
     std::thread th;
+    // Completions reported by a host function at the end of each request's
+    // stream work; the worker wakes on them instead of polling.
+    std::atomic<uint64_t> signals{0};
+    uint64_t seen = 0;
+    std::map<std::tuple<int, int, int, int>, uint64_t> est_cache;   // request_bytes per shape (worker only)
+
+    static void CUDART_CB on_done(void* self) {   // no CUDA calls and no lock in here
+        Server* sv = static_cast<Server*>(self);
+        sv->signals.fetch_add(1, std::memory_order_release);
+        sv->cv_work.notify_one();
+    }
 
     explicit Server(sift3d_ctx* c) : ctx(c) {
         budget = c->p.hbm_budget_bytes ? c->p.hbm_budget_bytes : (40ull << 30);
@@ -237,7 +249,10 @@ struct Server {
             cudaEventSynchronize(r->done);
             cudaEventDestroy(r->done);
         }
-        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+        for (cudaStream_t s : streams) {
+            cudaStreamSynchronize(s);   // each request's completion host function has run
+            cudaStreamDestroy(s);
+        }
         pool.clear();
     }
 
@@ -247,6 +262,19 @@ struct Server {
         if (*rc != SIFT3D_OK) return 0;
         const size_t cap = (size_t)std::max(ctx->p.max_keypoints, 1);
         return pl.bytes + cap * (sizeof(sift3d_keypoint) * 2 + 8 + 64) + (size_t)nx * ny * nz * 4 + (1 << 20);
+    }
+
+    // request_bytes of a shape that planned once (the worker thread only).
+    uint64_t estimate(const Request& r, std::string* err, int* rc) {
+        const auto key = std::make_tuple(r.nx, r.ny, r.nz, r.dtype);
+        auto it = est_cache.find(key);
+        if (it != est_cache.end()) {
+            *rc = SIFT3D_OK;
+            return it->second;
+        }
+        const uint64_t b = request_bytes(r.nx, r.ny, r.nz, r.dtype, err, rc);
+        if (*rc == SIFT3D_OK) est_cache.emplace(key, b);
+        return b;
     }
 
     std::unique_ptr<ServeBuffers> take_buffers(const Request& r, std::string* err, int* rc) {
@@ -308,18 +336,21 @@ struct Server {
         }
     }
 
-    int admit(Request* r) {
+    // Runs on the worker thread without the lock: it touches only worker-owned
+    // members (pool, streams, used, pooled) and fields of r that API threads
+    // read after the worker publishes r's state under the lock.  Returns true
+    // when r holds buffers and is running on the device.
+    bool admit(Request* r) {
         std::string err;
         int rc = SIFT3D_OK;
-        const uint64_t est = request_bytes(r->nx, r->ny, r->nz, r->dtype, &err, &rc);
+        const uint64_t est = estimate(*r, &err, &rc);
         evict_for(est);
         r->buf = take_buffers(*r, &err, &rc);
         if (!r->buf) {
             r->status = rc == SIFT3D_OK ? SIFT3D_ECUDA : rc;
             r->err = err;
             r->t_admit = r->t_done = now_ms();
-            r->state = Request::FAILED;
-            return r->status;
+            return false;
         }
         used += r->buf->bytes;
         if (streams.empty()) {
@@ -355,15 +386,16 @@ struct Server {
                 e = cudaEventRecord(r->done, r->stream);
                 if (e != cudaSuccess) rc = SIFT3D_ECUDA, err = cudaGetErrorString(e);
             }
+            // wake the worker when the stream gets here (without it the worker
+            // still finds the event complete at its next timed wake-up)
+            if (rc == SIFT3D_OK) (void)cudaLaunchHostFunc(r->stream, &Server::on_done, this);
         }
         r->t_admit = now_ms();
         if (rc != SIFT3D_OK) {
             r->status = rc;
             r->err = err;
         }
-        r->state = Request::RUNNING;
-        running.push_back(r);
-        return rc;
+        return true;
     }
 
     void retire(Request* r) {
@@ -395,7 +427,8 @@ struct Server {
         cudaSetDevice(ctx->device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
-            bool progressed = false;
+            bool progressed = false, budget_blocked = false;
+            seen = signals.load(std::memory_order_acquire);   // a later signal re-runs this loop
             for (size_t i = 0; i < running.size();) {
                 Request* r = running[i];
                 const cudaError_t q = r->status == SIFT3D_OK ? cudaEventQuery(r->done) : cudaSuccess;
@@ -416,10 +449,21 @@ struct Server {
                 Request* r = queue.front();
                 std::string err;
                 int rc = SIFT3D_OK;
-                const uint64_t est = request_bytes(r->nx, r->ny, r->nz, r->dtype, &err, &rc);
-                if (used + est > budget && !running.empty()) break;   // wait for memory to free up
+                const uint64_t est = estimate(*r, &err, &rc);
+                if (used + est > budget && !running.empty()) {   // wait for memory to free up
+                    budget_blocked = true;
+                    break;
+                }
                 queue.pop_front();
-                admit(r);
+                lk.unlock();   // the CUDA calls of admission run without the lock
+                const bool on_device = admit(r);
+                lk.lock();
+                if (on_device) {
+                    r->state = Request::RUNNING;
+                    running.push_back(r);
+                } else {
+                    r->state = Request::FAILED;
+                }
                 progressed = true;
             }
             if (progressed) cv_done.notify_all();
@@ -427,7 +471,12 @@ struct Server {
             if (running.empty() && queue.empty()) {
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
             } else if (!progressed) {
-                cv_work.wait_for(lk, std::chrono::microseconds(20));
+                // a completion signal, new work, or (a signal lost between the
+                // check and the wait) the next timed wake-up
+                cv_work.wait_for(lk, std::chrono::microseconds(200), [&] {
+                    return stop || signals.load(std::memory_order_acquire) != seen ||
+                           (!budget_blocked && !queue.empty() && (int)running.size() < ctx->p.max_inflight);
+                });
             }
         }
     }
