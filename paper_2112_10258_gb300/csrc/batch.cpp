@@ -158,7 +158,7 @@ int build_batch(const sift3d_params& p, const std::vector<std::array<int, 3>>& d
                 int nx_max = 0;
                 for (size_t i = 0; i < in_o.size(); ++i) {
                     const int v = in_o[i];
-                    LevelArgs la = level_args(bx->vols[v].ws, o, s, nullptr, dtype, bx->fuse_blur);
+                    LevelArgs la = level_args(bx->vols[v].ws, o, s, nullptr, dtype, bx->fuse_blur, false);
                     la.xy.row_tile = 16;
                     if (i == 0) first = la;
                     if (la.radius != first.radius || la.src_kind != first.src_kind || la.sub != first.sub ||

@@ -79,6 +79,8 @@ struct ConvZArgs {
     const float* src2;        // if set: z pass of this second intermediate with taps2
     void* dst2;               //   into dst2 (the pre-blurred level for the descriptors)
     Taps taps2;
+    float* sub_dst;           // if set (float32 storage, level S): also write the next
+    int64_t sub_py, sub_pz;   //   octave's G_0, the 2x2x2 means of G_s, with these pitches
 };
 
 // ---- peak detection + compaction --------------------------------------------

@@ -458,7 +458,15 @@ bool make_peak_tma_args(const Workspace& ws, int o, int first_scale, int ns, Pea
     return r == CUDA_SUCCESS;
 }
 
-LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype, bool fuse_blur) {
+// Whether the level-S z pass of octave o writes octave o+1's G_0 (float32
+// storage, rows that fit one CTA pair); the next octave's first y/x pass then
+// reads that G_0 instead of sub-sampling G_S itself.
+static bool z_writes_next_base(const Plan& pl, int o) {
+    return pl.p.storage == SIFT3D_STORAGE_F32 && o + 1 < pl.nO && pl.oct[o].py <= 256;
+}
+
+LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype, bool fuse_blur,
+                     bool z_sub) {
     const Plan& pl = ws.plan;
     const OctaveGeom& g = pl.oct[o];
     LevelArgs la;
@@ -482,6 +490,13 @@ LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int d
         xa.zero_count = ws.count;
         xa.taps = pl.t_init;
         la.radius = pl.r_init;
+    } else if (s == 1 && o > 0 && z_sub && z_writes_next_base(pl, o - 1)) {
+        // G_0 written by the previous octave's level-S z pass
+        xa.src = ws.G(o, 0);
+        xa.src_py = g.py;
+        xa.src_pz = g.pz;
+        xa.taps = pl.t_inc[0];
+        la.radius = pl.r_inc[0];
     } else if (s == 1 && o > 0) {   // sub-sample of the previous octave's level S
         la.sub = true;
         xa.src = ws.G(o - 1, pl.S);
@@ -522,6 +537,11 @@ LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int d
         za.dog = static_cast<float*>(ws.D(o, s - 1));
     }
     za.res = ws.Res(o);
+    if (z_sub && s == pl.S && z_writes_next_base(pl, o)) {
+        za.sub_dst = static_cast<float*>(ws.G(o + 1, 0));
+        za.sub_py = pl.oct[o + 1].py;
+        za.sub_pz = pl.oct[o + 1].pz;
+    }
     if (la.fused_blur) {
         za.src2 = ws.TB(o, s - 1);
         za.dst2 = ws.B(o, s - 1);
@@ -560,7 +580,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
         const OctaveGeom& g = pl.oct[o];
         int prev = -1;  // node that produced G_{s-1}
         for (int s = (o == 0 ? 0 : 1); s < pl.L; ++s) {
-            LevelArgs la = level_args(ws, o, s, c.input, c.dtype, false);
+            LevelArgs la = level_args(ws, o, s, c.input, c.dtype, false, true);
             ConvXYArgs& xa = la.xy;
             const int src_kind = la.src_kind, radius = la.radius;
             const bool sub = la.sub;
@@ -586,7 +606,9 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 // reads the intermediate, writes G_s; with the DoG also reads
                 // G_{s-1} and writes D_{s-1}; with the fused pre-blur also reads
                 // its intermediate and writes the pre-blurred level
-                tag(prev, "o%d.s%d.%s", o, s, 4 * N + e * N + (s > 0 ? (e + ed) * N : 0) + (za.dst2 ? (4 + e) * N : 0));
+                tag(prev, "o%d.s%d.%s", o, s,
+                    4 * N + e * N + (s > 0 ? (e + ed) * N : 0) + (za.dst2 ? (4 + e) * N : 0) +
+                        (za.sub_dst ? (uint64_t)pl.oct[o + 1].voxels() * e : 0));   // + the next G_0
             }
             g_node[o][s] = prev;
         }

@@ -125,7 +125,10 @@ struct LevelArgs {
     int radius = 0, src_kind = 2;   // src_kind: 0 float32 input, 1 uint8 input, 2 a pyramid level
     bool sub = false, fused_blur = false;
 };
-LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype, bool fuse_blur);
+// z_sub: the level-S z pass also writes the next octave's G_0 where it can
+// (the single-volume detect), and the next octave's first y/x pass reads it.
+LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int dtype, bool fuse_blur,
+                     bool z_sub);
 
 // Build the detect DAG (topologically ordered).  first_node / sort_node index
 // the two nodes that carry caller pointers.
