@@ -8,14 +8,16 @@
 //            In sub-sample mode the staged values are the 2x2x2 means of the
 //            previous octave's level S (Sec. 2.2.2 "Sub-sampling"), and the
 //            tile's own means are written out as the octave's G_0.
-//   conv_xy_row  (rows up to 256 wide) one CTA per 16 full rows of a plane,
-//            column pairs in the y pass and row pairs in the x pass, each tap
-//            one paired FP32 FMA (see below).
+//   conv_xy_row  (rows up to 256 wide) one CTA per 8 or 16 full rows of a
+//            plane, column pairs in the y pass and row pairs in the x pass, each
+//            tap one paired FP32 FMA (see below).
 //   conv_z   one thread per two adjacent columns and TZ outputs along z: the
 //            TZ + 2R inputs are loaded into registers (clamped z) and the TZ
 //            outputs accumulate from registers.  The epilogue stores G_s and the
 //            difference of Gaussians D_{s-1} = G_{s-1} - G_s (Sec. 2.2.2
-//            "Difference-of-Gaussian") so the DoG costs no extra pass.
+//            "Difference-of-Gaussian") so the DoG costs no extra pass; at level S
+//            (float32 storage) a variant also writes the next octave's G_0.
+//   *_batch  the same bodies over the tiles of many volumes in one launch.
 //
 // Every 1D pass is out[i] = sum_{k=-R..R} w_|k| in[clamp(i+k)], summed in
 // ascending k, in float32.
