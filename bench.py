@@ -593,6 +593,9 @@ def main():
     kbuf, brief, rrief = kbufs[0], briefs[0], rriefs[0]
     _, n_kp = det.detect(d_vol, capacity=CAPACITY, out=kbuf)   # also builds the graph
     kbuf_first = kbuf.clone()
+    kp_first = S.keypoints_to_numpy(kbuf_first, min(n_kp, CAPACITY))
+    kp_counts = {f"o{o}": [int(np.sum((kp_first["octave"] == o) & (kp_first["scale"] == s))) for s in (1, 2, 3)]
+                 for o in sorted(set(int(v) for v in kp_first["octave"]))}
 
     def step():
         det.detect(d_vol, capacity=CAPACITY, out=kbuf, sync=False)
@@ -769,7 +772,7 @@ def main():
         return
     base = None
     if world == 1 and not args.no_cpu_baseline:
-        kp = S.keypoints_to_numpy(kbuf_first, n_kp)
+        kp = kp_first
         gpu_keys = {(int(k["octave"]), int(k["scale"]), int(k["iz"]), int(k["iy"]), int(k["ix"])) for k in kp}
         base = cpu_baseline(vol, gpu_keys if args.storage == "f32" else None)
 
@@ -777,7 +780,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_volume": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
-        "data": "synthetic", "config": workload_config({"keypoints": n_kp,
+        "data": "synthetic", "config": workload_config({"keypoints": n_kp, "keypoints_by_octave_scale": kp_counts,
                                                         "launch": "direct" if args.eager else "CUDA graph",
                                                         "storage": args.storage, "inflight": P, "l2": l2_note}),
         "roofline": roofline,

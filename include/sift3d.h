@@ -118,7 +118,9 @@ typedef struct sift3d_params {
     int32_t  sign_sum_min;       /* 80 = strict extremum; 1..80                */
     int32_t  border;             /* 1, >= 1                                    */
     int32_t  profile;            /* 0; 1 = time every detect kernel with CUDA
-                                    events (sift3d_stage_times)                */
+                                    events (sift3d_stage_times).  The
+                                    environment variable SIFT3D_PROFILE=1 sets
+                                    it for every context sift3d_create makes. */
     double   contrast_thresh;    /* 0.005 (compared in float32 on the device)  */
     double   curvature_r;        /* 10, > 1                                    */
     double   trunc;              /* 4.0  filter radius = ceil(trunc * sigma)   */

@@ -1,6 +1,7 @@
 // extern "C" entry points of include/sift3d.h and the serving scheduler.
 #include <chrono>
 #include <atomic>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -540,6 +541,9 @@ int sift3d_create(const sift3d_params* params, sift3d_ctx** out) {
     auto* c = new (std::nothrow) sift3d_ctx();
     if (!c) return SIFT3D_ENOMEM;
     c->p = *params;
+    if (const char* env = std::getenv("SIFT3D_PROFILE")) {   // per-stage timing without code changes
+        if (env[0] == '1') c->p.profile = 1;
+    }
     c->test_timeouts_left = params->test_wait_timeout;
     make_pattern(c->p, c->pattern);
     *out = c;
