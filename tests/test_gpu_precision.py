@@ -4,7 +4,7 @@ and descriptor agreement against the FP64 oracle on brain-like 145x174x145
 volumes.  The 16-seed report is tests/precision_report.py; these tests hold
 the floors on two seeds.
 
-Floors.  FP16: the benchmark spec's target, recall and precision >= 0.99.  Both
+Floors.  FP16: the stated target, recall and precision >= 0.99.  Both
 types: at least the recall and precision that the oracle's FP64 emulation of the
 same storage arithmetic (build_pyramid_stored: levels rounded when stored,
 residual-corrected DoG) reaches on the same volume, less 0.01 for the float32

@@ -23,7 +23,7 @@ import pytest
 from oracle import sift3d_oracle as O
 from workloads.volumes import blob_volume, brain_like_volume
 
-REL = 1e-5                 # the spec comparison tolerance (relative to local magnitude)
+REL = 1e-5                 # the comparison tolerance (relative to the local magnitude)
 # A voxel flagged for a near comparison or a near contrast cut must flip under
 # C_TIGHT times the allowance: those margins are exact, and the allowance of the
 # two values of a comparison adds up to 0.7-1.0 of the tolerance.  A voxel
