@@ -523,6 +523,28 @@ def run_match(args, rank, world, local):
 
 
 # ------------------------------------------------------- matching on known pairs
+def similarity_transform(shape_zyx, scale, deg, t):
+    """(forward map of (x, y, z) points, warp of a (z, y, x) volume) for
+    T(p) = scale * R_z(deg) (p - c) + c + t, c the volume centre: the warp
+    returns B with B(T(p)) = A(p), trilinear, edge values outside."""
+    import scipy.ndimage as ndi
+    nz, ny, nx = shape_zyx
+    c = np.array([(nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2])
+    th = np.deg2rad(deg)
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    t = np.asarray(t, dtype=np.float64)
+    P = np.array([[0, 0, 1], [0, 1, 0], [1, 0, 0]], dtype=np.float64)   # (x, y, z) <-> (z, y, x)
+    Minv = R.T / scale                                  # p = Minv (q - c - t) + c
+
+    def forward(pts_xyz):
+        return (scale * (R @ (np.asarray(pts_xyz, np.float64) - c).T)).T + c + t
+
+    def warp(A):
+        return ndi.affine_transform(np.asarray(A, np.float64), P @ Minv @ P, offset=P @ (c - Minv @ (c + t)),
+                                    order=1, mode="nearest")
+    return forward, warp
+
+
 def run_pairs(args, rank, world, local):
     """Descriptor matching on synthetic pairs with a known similarity transform
     (the paper's matching comparison, Sec. 3.5.2, needs OASIS pairs and a Hough
@@ -535,13 +557,9 @@ def run_pairs(args, rank, world, local):
     if rank != 0:
         return
     import torch
-    import scipy.ndimage as ndi
     import paper_2112_10258_gb300 as S
     from workloads.volumes import brain_like_volume
     A = brain_like_volume(seed=3)
-    nz, ny, nx = A.shape
-    c = np.array([(nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2])
-    P = np.array([[0, 0, 1], [0, 1, 0], [1, 0, 0]], dtype=np.float64)   # (x, y, z) <-> (z, y, x)
 
     def describe_all(vol):
         det = S.Sift3D()
@@ -560,16 +578,11 @@ def run_pairs(args, rank, world, local):
     rng = np.random.default_rng(11)
     results = []
     for name, sc, deg, t in transforms:
-        th = np.deg2rad(deg)
-        R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
-        t = np.asarray(t, dtype=np.float64)
-        Minv = R.T / sc                                   # p = Minv (q - c - t) + c
-        B = ndi.affine_transform(A.astype(np.float64), P @ Minv @ P, offset=P @ (c - Minv @ (c + t)), order=1,
-                                 mode="nearest").astype(np.float32)
+        forward, warp = similarity_transform(A.shape, sc, deg, t)
+        B = warp(A).astype(np.float32)
         B += rng.normal(0, 0.01, B.shape).astype(np.float32)
         kb, bb, rb, sb = describe_all(B)
-        pa = np.stack([ka["x"], ka["y"], ka["z"]], 1).astype(np.float64)
-        ta = (sc * (R @ (pa - c).T)).T + c + t           # where each keypoint of A should be in B
+        ta = forward(np.stack([ka["x"], ka["y"], ka["z"]], 1))   # where each keypoint of A should be in B
         tol = 1.5 * (1 << ka["octave"].astype(np.int64)) * max(1.0, sc)
         row = {"transform": name, "keypoints_a": int(ka.size), "keypoints_b": int(kb.size)}
         for dname, kind, da, db in (("brief", S.DESC_BRIEF, ba, bb), ("rrief", S.DESC_RRIEF, ra, rb),
