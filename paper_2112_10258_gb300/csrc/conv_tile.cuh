@@ -1,5 +1,5 @@
-// Tile body of the y/x pass for rows wider than 256 (see conv.cu) and the
-// constants the conv kernels share.
+// Tile body of the y/x pass for rows wider than 256 (instantiated in
+// conv_xy_tile.cu) and the constants the conv kernels share.
 #pragma once
 
 #include "common.cuh"
