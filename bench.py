@@ -466,6 +466,19 @@ def run_serving(args, rank, world, local):
         by_shape.setdefault("x".join(map(str, shp)), []).append(lat[i])
     vps = len(arrivals) / wall
     vps = _max_over_ranks(dist, -vps) if dist is not None else vps
+    # where the tail comes from: each request's latency beside the number of
+    # other requests whose [arrival, arrival + latency] interval overlapped it
+    t_a = np.array([a for a, _ in arrivals])
+    t_b = t_a + lat / 1e3
+    overlap = np.array([int(np.sum((t_a < t_b[i]) & (t_b > t_a[i]))) - 1 for i in range(len(arrivals))])
+    tail = lat >= np.percentile(lat, 99)
+    shapes = np.array(["x".join(map(str, shp)) for _, shp in arrivals])
+    alone_vs_shared = {}
+    for k in by_shape:
+        a = lat[(shapes == k) & (overlap == 0)]
+        b = lat[(shapes == k) & (overlap > 0)]
+        alone_vs_shared[k] = {"alone_n": int(a.size), "alone_p50_ms": float(np.percentile(a, 50)) if a.size else None,
+                              "shared_n": int(b.size), "shared_p50_ms": float(np.percentile(b, 50)) if b.size else None}
     if rank == 0:
         line = {"mode": "serving", "metric": "serving p50/p99 latency (ms) and volumes/s, Poisson arrivals",
                 "value": float(np.percentile(lat, 50)), "unit": "ms (p50)", "p50_ms": float(np.percentile(lat, 50)),
@@ -477,6 +490,9 @@ def run_serving(args, rank, world, local):
                 "per_shape_p50_p99_ms": {k: [float(np.percentile(v, 50)), float(np.percentile(v, 99))]
                                          for k, v in by_shape.items()},
                 "keypoints_mean": float(kps.mean()),
+                "tail": {"overlapped_share_of_p99_tail": float(np.mean(overlap[tail] > 0)),
+                         "overlapped_share_of_all": float(np.mean(overlap > 0)),
+                         "per_shape_alone_vs_overlapped": alone_vs_shared},
                 "config": {"workload": "Poisson arrivals, sizes 64^3 / 145x174x145 / 256x256x192 equally likely, "
                                        "uint8 brain-like volumes in pinned host memory", "budget_gb": 40,
                            "max_inflight": 8, "api": "sift3d_submit(NOCOPY) / sift3d_poll; results read on host"},
