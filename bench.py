@@ -58,8 +58,9 @@ def parse():
                     help="detect: time only the headline phase (for ncu captures)")
     ap.add_argument("--eager", action="store_true", help="direct launches instead of the CUDA graph")
     ap.add_argument("--row-tile", type=int, choices=[0, 8, 16], default=0,
-                    help="y/x pass rows per CTA: 0 = autotuned at the first detect; 8 or 16 = fixed, no "
-                         "tuning launches (for ncu captures of a known launch order)")
+                    help="y/x pass rows per CTA: 0 = autotuned at the first detect; 8 or 16 = fixed, and the z "
+                         "pass at 16 outputs per thread, no tuning launches (for ncu captures of a known launch "
+                         "order)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="volumes processed concurrently (separate contexts/streams, distinct inputs)")
     ap.add_argument("--mode", choices=["headline", "batched", "serving", "match", "pairs"], default="headline",
@@ -683,7 +684,7 @@ def main():
     # ---- phase 1: the full hot path (detect + describe), graph launch path
     use_graphs = 0 if args.eager else 1
     P = max(1, args.inflight)
-    tile_kw = {"conv_row_tile": args.row_tile, "autotune": 0} if args.row_tile else {}
+    tile_kw = {"conv_row_tile": args.row_tile, "conv_z_tile": 16, "autotune": 0} if args.row_tile else {}
     dets = [S.Sift3D(storage=storage, use_graphs=use_graphs, **tile_kw) for _ in range(P)]
     det = dets[0]
     kbufs = [torch.empty(CAPACITY * 48, dtype=torch.uint8, device="cuda") for _ in range(P)]

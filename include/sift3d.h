@@ -157,12 +157,19 @@ typedef struct sift3d_params {
     int32_t  autotune;           /* 1 (default): at the first detect of a
                                     volume shape (outside stream capture),
                                     time each full-row y/x pass at tile
-                                    heights of 8 and 16 rows with CUDA events
-                                    and keep the faster (cached per process);
-                                    results are bitwise the same for either
-                                    height.  0 = 16 rows.                    */
+                                    heights of 8 and 16 rows, and each float32
+                                    z pass at 8 and 16 outputs per thread,
+                                    with CUDA events and keep the faster
+                                    (cached per process); results are bitwise
+                                    the same for either choice.  0 = 16 rows
+                                    and 16 outputs.                           */
     int32_t  conv_row_tile;      /* 0 (default): as autotune says; 8 or 16 =
                                     rows per CTA of the y/x pass              */
+    int32_t  conv_z_tile;        /* 0 (default): as autotune says; 8 or 16 =
+                                    outputs per thread of the z pass (float32
+                                    storage; 16-bit storage uses 16): the z
+                                    halo of 2R planes is re-read per that many
+                                    outputs                                   */
 } sift3d_params;
 
 /* A detected keypoint (48 bytes).  x,y,z are input-voxel coordinates of the

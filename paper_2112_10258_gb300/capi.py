@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("pattern_seed", C.c_uint64), ("storage", C.c_int32), ("use_graphs", C.c_int32),
         ("hbm_budget_bytes", C.c_uint64), ("max_keypoints", C.c_int32), ("max_inflight", C.c_int32),
         ("refine", C.c_int32), ("test_wait_timeout", C.c_int32), ("autotune", C.c_int32),
-        ("conv_row_tile", C.c_int32),
+        ("conv_row_tile", C.c_int32), ("conv_z_tile", C.c_int32),
     ]
 
 

@@ -512,6 +512,7 @@ int sift3d_default_params(sift3d_params* out) {
     out->test_wait_timeout = 0;
     out->autotune = 1;
     out->conv_row_tile = 0;
+    out->conv_z_tile = 0;
     out->refine = 0;
     return SIFT3D_OK;
 }

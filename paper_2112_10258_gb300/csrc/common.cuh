@@ -81,6 +81,7 @@ struct ConvZArgs {
     Taps taps2;
     float* sub_dst;           // if set (float32 storage, level S): also write the next
     int64_t sub_py, sub_pz;   //   octave's G_0, the 2x2x2 means of G_s, with these pitches
+    int z_tile;               // outputs per thread: 8 or 16 (float32 storage), else 16
 };
 
 // ---- peak detection + compaction --------------------------------------------

@@ -55,7 +55,7 @@ __device__ __forceinline__ void load_z_window(const float2* src, int64_t pz2, in
 }
 
 // A: ConvZArgs, or the batched ZVol (the same field names, no taps).
-template <int R, typename S, int RB, class A>
+template <int R, typename S, int RB, class A, int TZ = Z_TZ>
 __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps& taps2, int pb, int zt) {
     using P = Pair<S>;
     using PT = typename P::T;
@@ -63,24 +63,24 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
     const int64_t pair = (int64_t)pb * Z_THREADS + threadIdx.x;
     const int64_t pz2 = a.pz / 2;
     if (pair >= pz2) return;
-    const int z0 = zt * Z_TZ;
-    const bool interior = z0 - R >= 0 && z0 + Z_TZ + R <= a.nz;
+    const int z0 = zt * TZ;
+    const bool interior = z0 - R >= 0 && z0 + TZ + R <= a.nz;
     const bool with_dog = a.dog != nullptr;
     const bool with_res = a.res != nullptr;   // 16-bit storage of a level (null: descriptor pre-blur)
-    float2 v[Z_TZ + 2 * R];
-    load_z_window<Z_TZ + 2 * R, R>(reinterpret_cast<const float2*>(a.src) + pair, pz2, z0, a.nz, interior, v);
+    float2 v[TZ + 2 * R];
+    load_z_window<TZ + 2 * R, R>(reinterpret_cast<const float2*>(a.src) + pair, pz2, z0, a.nz, interior, v);
     // G_{s-1} as computed, before its rounding to storage: the stored value plus
     // its rounding residual (16-bit storage), so that the DoG carries no
     // storage rounding of G_{s-1}
-    float2 pv[Z_TZ];
+    float2 pv[TZ];
     const PT* prev = static_cast<const PT*>(a.prev) + pair;
     __half2* res = reinterpret_cast<__half2*>(a.res) + pair;
     if (with_dog) {
-        if (z0 + Z_TZ <= a.nz) {   // walk the planes
+        if (z0 + TZ <= a.nz) {   // walk the planes
             const PT* q = prev + (int64_t)z0 * pz2;
             const __half2* rq = res + (int64_t)z0 * pz2;
 #pragma unroll
-            for (int j = 0; j < Z_TZ; ++j) {
+            for (int j = 0; j < TZ; ++j) {
                 pv[j] = P::get(*q);
                 q += pz2;
                 if constexpr (narrow) {
@@ -91,7 +91,7 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < Z_TZ; ++j) {
+            for (int j = 0; j < TZ; ++j) {
                 const int64_t zo = (int64_t)min(z0 + j, a.nz - 1) * pz2;
                 pv[j] = P::get(prev[zo]);
                 if constexpr (narrow) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
     float2* dog = reinterpret_cast<float2*>(a.dog) + pair + (int64_t)z0 * pz2;
     __half2* rout = res + (int64_t)z0 * pz2;
 #pragma unroll
-    for (int j = 0; j < Z_TZ; ++j) {
+    for (int j = 0; j < TZ; ++j) {
         if (z0 + j >= a.nz) break;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -124,12 +124,12 @@ __device__ __forceinline__ void z_body(const A& a, const Taps& taps, const Taps&
         rout += pz2;
     }
     if constexpr (RB > 0) {   // the fused descriptor pre-blur, after the level so registers are reused
-        float2 u[Z_TZ + 2 * RB];
-        load_z_window<Z_TZ + 2 * RB, RB>(reinterpret_cast<const float2*>(a.src2) + pair, pz2, z0, a.nz,
-                                         z0 - RB >= 0 && z0 + Z_TZ + RB <= a.nz, u);
+        float2 u[TZ + 2 * RB];
+        load_z_window<TZ + 2 * RB, RB>(reinterpret_cast<const float2*>(a.src2) + pair, pz2, z0, a.nz,
+                                         z0 - RB >= 0 && z0 + TZ + RB <= a.nz, u);
         PT* dst2 = static_cast<PT*>(a.dst2) + pair + (int64_t)z0 * pz2;
 #pragma unroll
-        for (int j = 0; j < Z_TZ; ++j) {
+        for (int j = 0; j < TZ; ++j) {
             if (z0 + j >= a.nz) break;
             float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll

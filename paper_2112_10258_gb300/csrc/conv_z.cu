@@ -10,9 +10,11 @@ namespace {
 
 using namespace conv_detail;
 
-template <int R, typename S, int RB>
+// TZ outputs per thread: 16, or 8 (float32 storage) where the autotuner finds
+// the shorter column faster; every output is the same chain either way.
+template <int R, typename S, int RB, int TZ>
 __global__ void __launch_bounds__(Z_THREADS) conv_z_kernel(const ConvZArgs a) {
-    z_body<R, S, RB, ConvZArgs>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y);
+    z_body<R, S, RB, ConvZArgs, TZ>(a, a.taps, a.taps2, blockIdx.x, blockIdx.y);
 }
 
 // z pass of level S (float32 storage, rows up to 256 wide) that also writes
@@ -85,7 +87,13 @@ const void* z_sub_func_table(int r, std::integer_sequence<int, Rs...>) {
 
 template <typename S, int... Rs>
 const void* z_func_table(int r, std::integer_sequence<int, Rs...>) {
-    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, S, 0>)...};
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, S, 0, Z_TZ>)...};
+    return fns[r - 1];
+}
+
+template <int... Rs>
+const void* z_func_table_short(int r, std::integer_sequence<int, Rs...>) {   // float32, 8 outputs per thread
+    const void* fns[] = {reinterpret_cast<const void*>(&conv_z_kernel<Rs + 1, float, 0, 8>)...};
     return fns[r - 1];
 }
 
@@ -104,10 +112,15 @@ LaunchSpec conv_z_spec(int radius, int storage, const ConvZArgs& a) {
         s.name = "conv_z_dog_sub";
         return s;
     }
-    if (storage == SIFT3D_STORAGE_F32) s.func = z_func_table<float>(radius, RadiusSeq{});
-    else if (storage == SIFT3D_STORAGE_F16) s.func = z_func_table<__half>(radius, RadiusSeq{});
-    else s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
-    s.grid = dim3((unsigned)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS), (a.nz + Z_TZ - 1) / Z_TZ, 1);
+    const int tz = storage == SIFT3D_STORAGE_F32 && a.z_tile == 8 ? 8 : Z_TZ;
+    if (storage == SIFT3D_STORAGE_F32) {
+        s.func = tz == 8 ? z_func_table_short(radius, RadiusSeq{}) : z_func_table<float>(radius, RadiusSeq{});
+    } else if (storage == SIFT3D_STORAGE_F16) {
+        s.func = z_func_table<__half>(radius, RadiusSeq{});
+    } else {
+        s.func = z_func_table<__nv_bfloat16>(radius, RadiusSeq{});
+    }
+    s.grid = dim3((unsigned)((a.pz / 2 + Z_THREADS - 1) / Z_THREADS), (a.nz + tz - 1) / tz, 1);
     s.block = dim3(Z_THREADS);
     s.smem = 0;
     s.name = a.dog ? "conv_z_dog" : "conv_z";

@@ -81,6 +81,8 @@ int validate_params(const sift3d_params& p, std::string* err) {
     if (p.autotune < 0 || p.autotune > 1) return fail(err, "autotune must be 0 or 1");
     if (p.conv_row_tile != 0 && p.conv_row_tile != 8 && p.conv_row_tile != 16)
         return fail(err, "conv_row_tile must be 0, 8 or 16");
+    if (p.conv_z_tile != 0 && p.conv_z_tile != 8 && p.conv_z_tile != 16)
+        return fail(err, "conv_z_tile must be 0, 8 or 16");
 
     // filter radii of the schedule
     const int S = p.scales_per_octave;
@@ -532,6 +534,7 @@ LevelArgs level_args(const Workspace& ws, int o, int s, const void* input, int d
     za.ny = g.ny;
     za.nz = g.nz;
     za.taps = xa.taps;
+    za.z_tile = pl.p.conv_z_tile;
     if (s > 0) {
         za.prev = ws.G(o, s - 1);
         za.dog = static_cast<float*>(ws.D(o, s - 1));
@@ -601,6 +604,7 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
             }
             ConvZArgs& za = la.z;
             prev = add(conv_z_spec(radius, st, za), za, {nxy});
+            if (za.sub_dst == nullptr) nodes[prev].zk = {radius, true};
             {
                 const uint64_t N = (uint64_t)g.voxels();
                 // reads the intermediate, writes G_s; with the DoG also reads
@@ -659,7 +663,9 @@ std::vector<Node> build_detect(const Workspace& ws, const DetectCall& c, int* fi
                 za.ny = g.ny;
                 za.nz = g.nz;
                 za.taps = pl.t_desc;
+                za.z_tile = pl.p.conv_z_tile;
                 const int nz_ = add(conv_z_spec(pl.r_desc, st, za), za, {nxy});
+                nodes[nz_].zk = {pl.r_desc, true};
                 tag(nz_, "o%d.b%d.%s", o, s, (4 + e) * (uint64_t)g.voxels());
             }
         }
@@ -838,6 +844,57 @@ int tune_xy_node(Node& n, int storage, cudaStream_t st, std::string* err) {
     n.set_args(xa);
     return SIFT3D_OK;
 }
+
+// Outputs per thread of a float32 z pass (8 or 16) chosen by timing, per
+// (dims, radius, with DoG), for the whole process; as tune_xy_node.
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned_z;
+
+int tune_z_node(Node& n, int storage, cudaStream_t st, std::string* err) {
+    if (storage != SIFT3D_STORAGE_F32) return SIFT3D_OK;   // 16-bit storage has one depth
+    ConvZArgs za;
+    memcpy(&za, n.arg.data(), sizeof(za));
+    const auto key = std::make_tuple(za.nx, za.ny, za.nz, n.zk.radius, za.dog != nullptr ? 1 : 0);
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned_z.find(key);
+        if (it != g_tuned_z.end()) best = it->second;
+    }
+    if (best == 0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best_ms = 0.f;
+        for (int tz : {16, 8}) {
+            if (e != cudaSuccess) break;
+            za.z_tile = tz;
+            const LaunchSpec s = conv_z_spec(n.zk.radius, storage, za);
+            if (s.func == nullptr) continue;
+            void* args[1] = {&za};
+            e = launch_spec(s, args, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_spec(s, args, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (best == 0 || ms < best_ms)) best = tz, best_ms = ms;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) {
+            if (err) *err = std::string("autotune: ") + cudaGetErrorString(e);
+            return SIFT3D_ECUDA;
+        }
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tuned_z[key] = best;
+    }
+    memcpy(&za, n.arg.data(), sizeof(za));
+    za.z_tile = best;
+    n.spec = conv_z_spec(n.zk.radius, storage, za);
+    n.set_args(za);
+    return SIFT3D_OK;
+}
 }  // namespace
 
 int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_graph, bool profile,
@@ -851,19 +908,22 @@ int run_detect(Workspace& ws, DetectExec& ex, const DetectCall& c, bool use_grap
                 ex.nodes.clear();
                 return SIFT3D_EINVAL;
             }
-        // tile heights of the y/x passes: timed on this device unless fixed, or
-        // unless the stream is being captured (no synchronisation allowed there)
+        // tile heights of the y/x passes and depths of the z passes: timed on
+        // this device unless fixed, or unless the stream is being captured (no
+        // synchronisation allowed there)
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) (void)cudaGetLastError();
-        if (ws.plan.p.autotune && ws.plan.p.conv_row_tile == 0 && cap == cudaStreamCaptureStatusNone)
-            for (auto& n : ex.nodes)
-                if (n.xy.valid) {
-                    const int rc = tune_xy_node(n, ws.plan.p.storage, st, err);
-                    if (rc != SIFT3D_OK) {
-                        ex.nodes.clear();
-                        return rc;
-                    }
+        if (ws.plan.p.autotune && cap == cudaStreamCaptureStatusNone)
+            for (auto& n : ex.nodes) {
+                int rc = SIFT3D_OK;
+                if (n.xy.valid && ws.plan.p.conv_row_tile == 0) rc = tune_xy_node(n, ws.plan.p.storage, st, err);
+                if (n.zk.valid && ws.plan.p.conv_z_tile == 0 && rc == SIFT3D_OK)
+                    rc = tune_z_node(n, ws.plan.p.storage, st, err);
+                if (rc != SIFT3D_OK) {
+                    ex.nodes.clear();
+                    return rc;
                 }
+            }
         ex.cur_input = c.input;
         ex.cur_out = c.out;
         if (ex.profile) {

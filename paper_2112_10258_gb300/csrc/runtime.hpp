@@ -99,6 +99,10 @@ struct Node {
         int radius = 0, src_kind = 0;
         bool sub = false, valid = false;
     } xy;
+    struct ZKey {                          // a z pass node whose depth may be tuned
+        int radius = 0;
+        bool valid = false;
+    } zk;
     template <class A>
     void set_args(const A& a) {
         arg.assign((sizeof(A) + 7) / 8, 0ull);

@@ -325,14 +325,16 @@ def test_one_context_many_shapes_shares_its_arena(S):
 
 
 def test_tile_heights_and_autotune_are_bitwise_equal(S):
-    """The y/x pass's rows per CTA (8 or 16, or the autotuner's pick)
-    changes which CTA computes an output, never its summation: every level,
-    keypoint and descriptor is bitwise the same (also with the fused pre-blur
-    and the sub-sampling passes, and a second shape)."""
+    """The y/x pass's rows per CTA (8 or 16), the z pass's outputs per thread
+    (8 or 16), or the autotuner's picks change which thread computes an
+    output, never its summation: every level, keypoint and descriptor is
+    bitwise the same (also with the pre-blur and the sub-sampling passes, and
+    a second shape)."""
     for shape in ((145, 174, 145), (100, 90, 80)):
         vol = brain_like_volume(seed=12, shape=shape)
         outs = []
-        for kw in ({"conv_row_tile": 16, "autotune": 0}, {"conv_row_tile": 8}, {"autotune": 1}):
+        for kw in ({"conv_row_tile": 16, "conv_z_tile": 16, "autotune": 0}, {"conv_row_tile": 8},
+                   {"conv_z_tile": 8, "autotune": 0}, {"autotune": 1}):
             det, buf, n, kps = _run(S, vol, **kw)
             brief, rrief = det.describe(buf, n)
             lv = []
