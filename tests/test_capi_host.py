@@ -116,6 +116,8 @@ def test_pattern_matches_oracle_generator(lib, seed, method):
     ("curvature_r", 0.5), ("trunc", 0.0), ("desc_method", 0), ("desc_method", 6), ("storage", 3),
     ("max_inflight", 0),
     ("trunc", 10.0),   # radius ceil(10 * 3.09) > 16
+    ("autotune", 2), ("conv_row_tile", 12), ("conv_row_tile", 32), ("conv_z_tile", 4), ("conv_z_tile", 24),
+    ("test_wait_timeout", -1), ("refine", 2),
 ])
 def test_invalid_params_rejected(lib, field, value):
     p = lib.sift3d_default_params()
