@@ -11,8 +11,14 @@ Printed JSON line (rank 0):
   path_roofline  pyramid+DoG+peak path: byte model / time vs measured HBM peak
   roofline       the dominant kernel: its algorithmic bytes / mean duration
   e2e            same metric through sift3d_submit/poll with HOST buffers
-  cpu_baseline   the FP64 oracle timed on the host (bounded sample)
+  cpu_baseline   the FP64 oracle timed on the host (all cores and one core), and its
+                 keypoints compared with the CUDA path's
 L2 is flushed (512 MiB write) before every timed step, outside its events.
+
+Other modes: --mode batched (256 uneven volumes through sift3d_detect_batch),
+serving (a Poisson request stream through submit/poll, p50/p99), match
+(nearest-neighbour matching speed) and pairs (matching inliers on synthetic
+pairs with a known similarity transform).
 
 --impl reference runs the FP64 oracle as the reference arm on the host cores.
 Multi-GPU (torchrun): each rank processes its own volume (weak scaling); no
